@@ -1,0 +1,361 @@
+"""Benchmark: simultaneous matrix cos/sin on GB300.
+
+One step = the n = 4096 single-matrix workload: dense N(0,1) matrices with
+||A||_1 in {2^-4, 1, 8, 64}, plus a symmetric (A + A^T)/2 and a non-normal
+upper-triangular (strict upper part x10) matrix at ||A||_1 = 8, each through
+the FP64 path (double table) and, where built, the FP32 path (single table).
+Every matrix is an independent problem, so with N GPUs every rank runs the
+whole set (weak scaling, no collective on the data path).
+
+Prints one JSON line (see the repository's DESIGN notes for the fields).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 4096
+NORMS = [2.0 ** -4, 1.0, 8.0, 64.0]
+EXTRA = [("symmetric", 8.0), ("triangular", 8.0)]
+METRIC = "cos+sin TFLOP/s & matrices/s (n=4096, batched) at stated error vs FP64 oracle"
+WORKLOAD = ("n=4096 single matrices: N(0,1) at ||A||_1 in {2^-4,1,8,64} + symmetric and "
+            "upper-triangular(x10) at ||A||_1=8")
+
+
+def cases(precisions):
+    out = []
+    for prec in precisions:
+        for nrm in NORMS:
+            out.append((prec, "normal", nrm))
+        for fam, nrm in EXTRA:
+            out.append((prec, fam, nrm))
+    return out
+
+
+def make_input(fam, nrm, prec):
+    from paper_2010_00465_gb300 import inputs
+    A = inputs.matrix(N, fam, nrm, index=1)
+    return A.astype(np.float32) if prec == "fp32" else A
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [v for v in sm if v >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The oracle as it stands, on the host cores, on a bounded sample: FP64
+    n = 1024 N(0,1) matrices at ||A||_1 = 8 (2m = 24, s = 3: 13 products)."""
+    import oracle
+    from paper_2010_00465_gb300 import inputs
+    oracle.build()
+    n = 1024
+    A = inputs.matrix(n, "normal", 8.0, index=1)
+    t0 = time.perf_counter()
+    done = 0
+    flops = 0.0
+    while True:
+        _, _, info = oracle.cossin(A)
+        done += 1
+        flops += 2.0 * n ** 3 * info["products"]
+        if time.perf_counter() - t0 >= seconds_target or done >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d x oracle cos/sin of one n=%d FP64 N(0,1) matrix, ||A||_1=8 (2m=24, s=3), %.1f s"
+                      % (done, n, dt),
+            "matrices_per_s": done / dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2010_00465_gb300 import inputs
+    oracle.build()
+    n = 512
+    A = inputs.matrix(n, "normal", 8.0, index=1)
+    for _ in range(args.warmup):
+        oracle.cossin(A)
+    times, flops = [], 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, info = oracle.cossin(A)
+        times.append(time.perf_counter() - t0)
+        flops += 2.0 * n ** 3 * info["products"]
+    total = sum(times)
+    val = flops / total / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "n=512 FP64 ||A||_1=8 per step"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "one oracle cos/sin of a 512x512 FP64 N(0,1) matrix, ||A||_1=8, per step"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precisions", default=None, help="comma list: fp64,fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2010_00465_gb300 import api, _lib
+
+    precs = args.precisions.split(",") if args.precisions else available_precisions(api)
+    work = cases(precs)
+    # inputs resident in HBM, outputs and workspace preallocated
+    dev_in = [torch.from_numpy(make_input(f, r, p)).to(dev) for p, f, r in work]
+    outs = [(torch.empty_like(a), torch.empty_like(a)) for a in dev_in]
+    wsz = max(api.workspace_size(N, p) for p in precs)
+    wsp = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    infos = []
+
+    def step(record=False):
+        for (p, f, r), A, (C, S) in zip(work, dev_in, outs):
+            _, _, info = api.cossin(A, p, workspace=wsp, out=(C, S), return_info=True)
+            if record:
+                infos.append(info)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    flops_per_step = 0.0
+    step(record=True)
+    torch.cuda.synchronize()
+    flops_per_step = sum(i["flops"] for i in infos)
+    launches_per_step = sum(2 + i["products"] + (0 if p == "fp64" else extra_launches(p, i))
+                            for (p, _, _), i in zip(work, infos))
+
+    api.prof_reset()
+    api.prof_enable(True)
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    api.prof_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kern = {k: api.prof_read(k) for k in ("norm1", "gemm_f64", "gemm_tf32", "other")}
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    host_in = [torch.from_numpy(make_input(f, r, p)).pin_memory() for p, f, r in work]
+    h2d = sum(a.numel() * a.element_size() for a in host_in)
+    d2h = 2 * h2d
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 2))
+    for _ in range(e2e_steps):
+        for (p, _, _), A in zip(work, host_in):
+            C, S = api.cossin(A, p, workspace=wsp)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # accuracy stated beside the number: the 64 x 64 workload against the oracle,
+    # and cos^2 + sin^2 - I at n = 4096
+    acc = accuracy(api, dev_in, outs, work)
+
+    total_flops = flops_per_step * args.steps * ws
+    value = total_flops / (ms / 1e3) / 1e12
+    dominant = max(("gemm_f64", "gemm_tf32"), key=lambda k: kern[k][0])
+    kms, kn, kwork = kern[dominant]
+    clocks = clk.summary()
+    pk, pk_kind = peaks()
+    roof = roofline(dominant, kms, kn, kwork, pk, pk_kind, clocks)
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "+".join("f64" if p == "fp64" else "f32(3xtf32)" for p in precs),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "precisions": precs, "matrices_per_step": len(work),
+                   "l2": "inputs > L2: each step reads %d matrices of %d MB and streams GBs of workspace"
+                         % (len(work), N * N * 8 // 2 ** 20)},
+        "matrices_per_s": len(work) * args.steps * ws / (ms / 1e3),
+        "roofline": roof,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "e2e": {"value": flops_per_step * e2e_steps / e2e_s / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "accuracy": acc,
+        "per_case": [{"prec": p, "family": f, "norm1": r, "m": i["m"], "s": i["s"], "products": i["products"]}
+                     for (p, f, r), i in zip(work, infos)],
+        "kernels": {k: {"ms": v[0], "launches": v[1], "work": v[2]} for k, v in kern.items()},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def available_precisions(api):
+    precs = ["fp64"]
+    try:
+        import torch
+        a = torch.zeros(1, 1, dtype=torch.float32, device="cuda")
+        api.cossin(a, "fp32")
+        precs.append("fp32")
+    except Exception:
+        pass
+    return precs
+
+
+def extra_launches(prec, info):
+    return 2  # splitting A and the final recombination
+
+
+def roofline(kind, ms, launches, work, pk, pk_kind, clocks):
+    if launches == 0 or ms <= 0:
+        return None
+    per_launch_s = ms / 1e3 / launches
+    achieved = work / launches / per_launch_s / 1e12
+    if kind == "gemm_f64":
+        # FP64 FMA units: 2 per SM per clock (1.25 TFLOP/s at 2070 MHz over 152 SMs)
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak = 2 * 2 * 152 * mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "gemm_f64_kernel",
+                "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x median SM clock under load (%.0f MHz)" % mhz}
+    # TF32 tensor: half the bf16 rate (nominal 1.1 vs 2.25 PFLOP/s); three passes per product
+    bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    peak = bf16 * 1100.0 / 2250.0
+    issued = achieved * 3
+    return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
+            "traffic": None, "kernel": "gemm_tf32_kernel",
+            "peak_note": "%s sustained bf16 x nominal tf32/bf16 ratio; achieved counts the 3 TF32 passes"
+                         % pk_kind, "algorithmic_tflops": achieved}
+
+
+def accuracy(api, dev_in, outs, work):
+    import torch
+    import oracle
+    from paper_2010_00465_gb300 import inputs
+    res = {}
+    A = inputs.matrix(64, "normal", 2.0, index=0)
+    Co, So, _ = oracle.cossin(A)
+    C, S = api.cossin(torch.from_numpy(A).cuda(), "fp64")
+    res["fp64_64x64_rel_err_vs_oracle"] = max(
+        float(np.linalg.norm(C.cpu().numpy() - Co) / np.linalg.norm(Co)),
+        float(np.linalg.norm(S.cpu().numpy() - So) / np.linalg.norm(So)))
+    for (p, f, r), Ad, (C, S) in zip(work, dev_in, outs):
+        if f == "normal" and r == 64.0:
+            Cd, Sd = C.double(), S.double()
+            I = torch.eye(N, dtype=torch.float64, device=Cd.device)
+            R = Cd @ Cd + Sd @ Sd - I
+            res["%s_4096_norm64_pythagoras_residual" % p] = float(
+                R.norm() / ((Cd @ Cd).norm() + (Sd @ Sd).norm()))
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,134 @@
+/*
+ * cossin.h -- C ABI of the GB300 (sm_103a) library that computes cos(A) and
+ * sin(A) of a real dense n x n matrix together, by the method of Seydaoglu,
+ * Bader, Blanes and Casas, "Computing the matrix sine and cosine
+ * simultaneously with a reduced number of products" (arXiv:2010.00465).
+ *
+ * The method (paper section / equation in brackets):
+ *   1. theta = ||A||_1, the exact matrix 1-norm            [Sec. 4]
+ *   2. the family 2m in {4, 8, 16, 24} and the scaling s from the admissible
+ *      norms theta_2m of Table 1 (double) or Table 2 (single) [Sec. 3]
+ *   3. B = A_2 = (2^-s A)^2                                 [Sec. 1]
+ *   4. the factorised Taylor schemes, cos as T^c_2m(A_s) and sin as
+ *      A_s * p(A_2), with Pi_2m = 3, 4, 6, 7 products       [Sec. 2.1]
+ *   5. s double-angle steps C <- 2C^2 - I, S <- 2SC         [Sec. 1]
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense, row-major and contiguous (leading dimension n).
+ *     Because f(A^T) = f(A)^T for cos and sin, a column-major caller gets
+ *     column-major results from the same call.
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library never frees them.  The library allocates device memory only
+ *     where an entry point says so.
+ *   - Every call is asynchronous on `stream` except where stated; results
+ *     are ready once the stream is synchronised.  Argument errors are
+ *     detected before any work is queued and return a status without side
+ *     effects.  No C++ exception crosses this interface.
+ *   - On a status other than CS_OK, cossin_last_error() returns a message
+ *     for the calling thread.
+ *   - n = 0 is a valid no-op.  A = 0 gives C = I, S = 0.
+ */
+#ifndef COSSIN_H
+#define COSSIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream; NULL is the legacy default stream. */
+typedef struct CUstream_st* cossin_stream_t;
+
+typedef enum {
+  CS_OK = 0,
+  CS_EINVAL = 1,      /* bad argument: size, alias, precision, forced (m, s), workspace */
+  CS_ENOMEM = 2,      /* a device allocation made by the library failed */
+  CS_ENONFINITE = 3,  /* ||A||_1 is Inf or NaN */
+  CS_ERANGE = 4,      /* the scaling would need s > 64 */
+  CS_ECUDA = 5,       /* a CUDA runtime call failed (message has the CUDA error) */
+  CS_ETIMEOUT = 6     /* a device-side bounded wait expired (batched kernel) */
+} cs_status;
+
+typedef enum {
+  /* FP64 in and out; double table (u = 2^-53); every product in FP64. */
+  CS_FP64 = 0,
+  /* FP32 in and out; single table (u = 2^-24); every product as a
+   * three-pass TF32 tensor-core product (hi*hi + hi*lo + lo*hi) with FP32
+   * accumulation, linear combinations in FP32. */
+  CS_FP32 = 1,
+  /* FP64 in and out; single table; the Taylor chain (steps 3-4) as
+   * three-pass TF32 tensor-core products, while the norm, the choice of
+   * (m, s) and the double-angle steps run in FP64.  Accuracy is FP32-level. */
+  CS_SPLIT_TF32 = 2
+} cs_prec;
+
+/* What one call did. */
+typedef struct {
+  double norm1;      /* ||A||_1 as computed on the device (FP64) */
+  int32_t m;         /* 2m of the family used: 4, 8, 16 or 24 */
+  int32_t s;         /* double-angle steps */
+  int32_t products;  /* Pi_2m + 2 s matrix products */
+  int32_t table;     /* 0 = double table (Table 1), 1 = single table (Table 2) */
+  double flops;      /* algorithmic flops 2 n^3 (Pi_2m + 2 s) */
+} cs_info;
+
+/* Bytes of device workspace cossin_ex needs for one n x n matrix in `prec`.
+ * Host-only; never touches the GPU. */
+cs_status cossin_workspace_size(int64_t n, cs_prec prec, size_t* bytes);
+
+/* Steps 1-2 only.  theta = ||A||_1 of the device matrix A_dev (FP64 for
+ * CS_FP64 / CS_SPLIT_TF32, FP32 for CS_FP32), computed on the device with
+ * FP64 accumulation; blocks until it is on the host.  Uses a small
+ * library-owned device buffer (allocated on first use per device). */
+cs_status cossin_norm1(const void* A_dev, int64_t n, cs_prec prec, double* norm1,
+                       cossin_stream_t stream);
+
+/* Step 2 on the host: the (2m, s) of minimal cost Pi_2m + 2 s over the four
+ * families with ||A_s||_1 = theta / 2^s <= min(theta^c_2m, theta^s_2m)
+ * (Tables 1-2; ties go to the smaller s).  table: 0 double, 1 single. */
+cs_status cossin_select(double norm1, int32_t table, int32_t* m, int32_t* s);
+
+/* cos(A) and sin(A).  A_dev, C_dev, S_dev: n x n device matrices of the
+ * precision's element type (C and S must not overlap A or each other).
+ * Allocates its workspace with cudaMallocAsync on `stream` and frees it on
+ * the same stream; synchronises the stream once to read ||A||_1. */
+cs_status cossin(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, void* S_dev,
+                 cossin_stream_t stream);
+
+/* As cossin, with caller-provided workspace (ws_dev, at least
+ * cossin_workspace_size bytes, 256-byte aligned) so that nothing is
+ * allocated, and optional forced (m, s): force_m in {4, 8, 16, 24} together
+ * with force_s in [0, 64], or both -1 for the automatic choice (with a forced
+ * pair the norm is still computed and reported).  info may be NULL. */
+cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, void* S_dev,
+                    void* ws_dev, size_t ws_bytes, int32_t force_m, int32_t force_s,
+                    cs_info* info, cossin_stream_t stream);
+
+/* Last error message of the calling thread ("" if none). */
+const char* cossin_last_error(void);
+
+/* Kernel timing hooks used by the benchmark.  While enabled, the library
+ * records CUDA events around each launch of the kinds below on the launch
+ * stream; cossin_prof_read synchronises those events and returns the summed
+ * device time (ms), the number of launches and the algorithmic flops or
+ * bytes of those launches since the last reset. */
+typedef enum {
+  CS_KERNEL_NORM1 = 0,      /* bytes = n^2 * element size */
+  CS_KERNEL_GEMM_F64 = 1,   /* flops = 2 M N K */
+  CS_KERNEL_GEMM_TF32 = 2,  /* flops = 2 M N K (algorithmic, not the 3 passes) */
+  CS_KERNEL_BATCHED = 3,    /* flops = sum over matrices of 2 n^3 (Pi_2m + 2 s) */
+  CS_KERNEL_ADJOINT = 4,    /* flops = 2 M N K of the reverse-pass products */
+  CS_KERNEL_OTHER = 5,      /* splits and conversions; bytes moved */
+  CS_KERNEL_KINDS = 6
+} cs_kernel_kind;
+
+void cossin_prof_enable(int32_t on);
+void cossin_prof_reset(void);
+cs_status cossin_prof_read(int32_t kind, double* ms, int64_t* launches, double* work);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COSSIN_H */

@@ -1,0 +1,477 @@
+// cossin_api.cu -- host side of the library: argument checks, the choice of
+// (m, s), the product plans of the factorised Taylor schemes, the double-angle
+// recovery, workspace layout, error reporting and kernel timing hooks.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+#include "plan.h"
+
+namespace cs {
+
+// ---------------------------------------------------------------- errors ---
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+cs_status fail(cs_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+cs_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return CS_ECUDA;
+}
+
+// ------------------------------------------------------------- profiling ---
+namespace {
+struct ProfRecord {
+  int kind;
+  double work;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRecord> g_prof_pending;
+double g_prof_ms[CS_KERNEL_KINDS] = {};
+int64_t g_prof_n[CS_KERNEL_KINDS] = {};
+double g_prof_work[CS_KERNEL_KINDS] = {};
+}  // namespace
+
+ProfScope::ProfScope(int kind_, double work_, cudaStream_t stream_)
+    : kind(kind_), work(work_), stream(stream_) {
+  bool on;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    on = g_prof_on;
+  }
+  if (!on) return;
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+    ev[0] = ev[1] = nullptr;
+    return;
+  }
+  cudaEventRecord(ev[0], stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!ev[0]) return;
+  cudaEventRecord(ev[1], stream);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_pending.push_back({kind, work, ev[0], ev[1]});
+}
+
+static void prof_drain() {
+  std::vector<ProfRecord> pend;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    pend.swap(g_prof_pending);
+  }
+  for (auto& r : pend) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      g_prof_ms[r.kind] += ms;
+      g_prof_n[r.kind] += 1;
+      g_prof_work[r.kind] += r.work;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+}
+
+// -------------------------------------------------------------- selection ---
+// Admissible norms theta_2m of the new Taylor schemes: Table 1 (double,
+// u = 2^-53) and Table 2 (single, u = 2^-24), 2m = 4, 8, 16, 24.  Table 1's
+// k = 7 sine entry reads 1.97, but the printed k = 7 sine coefficients match
+// the series only through A^21; the Sec. 3 error series with them reaches
+// 2^-53 at 1.8555, the value used here.
+static const double kThetaCos[2][4] = {{6.5633e-3, 1.1495e-1, 9.8108e-1, 2.5675},
+                                       {1.8709e-1, 8.5756e-1, 2.9935, 5.5555}};
+static const double kThetaSin[2][4] = {{1.777e-2, 8.0438e-2, 1.1184, 1.8555},
+                                       {3.1386e-1, 7.492e-1, 3.2152, 4.3819}};
+static const int kFamilies[4] = {4, 8, 16, 24};
+static const int kProducts[4] = {3, 4, 6, 7};  // Pi_2m, Tables 1-2
+
+int products_of(int m) {
+  for (int f = 0; f < 4; ++f)
+    if (kFamilies[f] == m) return kProducts[f];
+  return -1;
+}
+
+cs_status select_ms(double norm1, int table, int* m, int* s) {
+  if (table < 0 || table > 1) return fail(CS_EINVAL, "select: table must be 0 (double) or 1 (single)");
+  if (!isfinite(norm1)) return fail(CS_ENONFINITE, "select: ||A||_1 is not finite");
+  if (norm1 < 0) return fail(CS_EINVAL, "select: negative norm");
+  int best = -1, best_s = 0, best_cost = 1 << 30;
+  for (int f = 0; f < 4; ++f) {
+    const double th = fmin(kThetaCos[table][f], kThetaSin[table][f]);
+    int sf = 0;
+    while (sf <= kMaxS && ldexp(norm1, -sf) > th) ++sf;
+    if (sf > kMaxS) continue;
+    const int cost = kProducts[f] + 2 * sf;
+    if (cost < best_cost || (cost == best_cost && sf < best_s)) {
+      best = f;
+      best_s = sf;
+      best_cost = cost;
+    }
+  }
+  if (best < 0) return fail(CS_ERANGE, "select: ||A||_1 needs more than 64 double-angle steps");
+  *m = kFamilies[best];
+  *s = best_s;
+  return CS_OK;
+}
+
+// ------------------------------------------------------------- workspace ---
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout make_layout(int64_t n, int prec) {
+  Layout L;
+  const size_t n2 = (size_t)n * (size_t)n;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.norm_partial = take(sizeof(double) * (size_t)norm1_scratch_elems(n));
+  L.norm_out = take(sizeof(double));
+  if (prec == CS_FP64) {
+    for (int w = 0; w < kWorkSlots; ++w) L.w[w] = take(sizeof(double) * n2);
+    L.ping64[0] = take(sizeof(double) * 2 * n2);
+    L.ping64[1] = take(sizeof(double) * 2 * n2);
+  } else {
+    L.a_hi = take(sizeof(float) * n2);
+    L.a_lo = take(sizeof(float) * n2);
+    for (int w = 0; w < kWorkSlots; ++w) {
+      L.w[w] = take(sizeof(float) * n2);
+      L.w_lo[w] = take(sizeof(float) * n2);
+    }
+    for (int p = 0; p < 2; ++p) {
+      L.ping32[p] = take(sizeof(float) * 2 * n2);
+      L.ping32_lo[p] = take(sizeof(float) * 2 * n2);
+    }
+    if (prec == CS_SPLIT_TF32) {
+      L.ping64[0] = take(sizeof(double) * 2 * n2);
+      L.ping64[1] = take(sizeof(double) * 2 * n2);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+// ------------------------------------------------------------------ plans ---
+// Products of the factorised schemes of Sec. 2.1, written as data.  Slot SL_A
+// is A itself, SL_C and SL_S receive T^c_2m(A_s) and the sine approximant,
+// W0..W7 hold intermediates.  Every step is P = X Y followed by its epilogue;
+// the first product folds the scaling (A_s)^2 = 4^-s A A and the last folds
+// A_s = 2^-s A into alpha.
+std::vector<Step> chain_plan(int m, int s) {
+  const double a2 = ldexp(1.0, -2 * s), as = ldexp(1.0, -s);
+  std::vector<Step> P;
+  auto out = [](int slot, double alpha, double gamma, std::vector<std::pair<int, double>> beta = {},
+                std::vector<std::pair<int, double>> delta = {}) {
+    return OutSpec{slot, alpha, gamma, std::move(beta), std::move(delta)};
+  };
+  P.push_back(Step{SL_A, SL_A, {out(W(0), a2, 0.0)}});  // A2 = (2^-s A)^2
+  if (m == 4) {
+    // eqs. Algorithm3cA, Algorithm3sA: T4c = I - A2/2! + A4/4!, T5s = A(I - A2/3! + A4/5!)
+    P.push_back(Step{W(0), W(0), {out(SL_C, 1.0 / 24, 1.0, {{W(0), -0.5}}),
+                                  out(W(1), 1.0 / 120, 1.0, {{W(0), -1.0 / 6}})}});
+    P.push_back(Step{SL_A, W(1), {out(SL_S, as, 0.0)}});
+  } else if (m == 8) {
+    // eqs. Algorithm4cA, Algorithm4sA: A8 = A4(-A2/6! + A4/8!),
+    // T8c = I - A2/2 + A4/24 + A8, T79s = A(I - A2/3! + A4/5! + (6!/7!) A8)
+    P.push_back(Step{W(0), W(0), {out(W(1), 1.0, 0.0),                                 // A4
+                                  out(W(2), 1.0 / 40320, 0.0, {{W(0), -1.0 / 720}}),   // -A2/6! + A4/8!
+                                  out(W(3), 1.0 / 24, 1.0, {{W(0), -0.5}}),            // I - A2/2 + A4/24
+                                  out(W(4), 1.0 / 120, 1.0, {{W(0), -1.0 / 6}})}});    // I - A2/6 + A4/120
+    P.push_back(Step{W(1), W(2), {out(SL_C, 1.0, 0.0, {{W(3), 1.0}}),
+                                  out(W(4), 720.0 / 5040.0, 0.0, {{W(4), 1.0}})}});
+    P.push_back(Step{SL_A, W(4), {out(SL_S, as, 0.0)}});
+  } else if (m == 16) {
+    // eq. Algorithm6cA with eq. cosm8, eq. Algorithm6sA with its z list.
+    const double r = sqrt(36681.0);
+    const double x1 = 7.0 / 500.0, x2 = -7.0 / 60000.0, x3 = (-1533.0 + 7.0 * r) / 2500.0;
+    const double x4 = -5.0 * (124581.0 + 391.0 * r) / 10594584.0, x5 = 9775.0 / 10594584.0;
+    const double x6 = -5.0 * (1001.0 + r) / 508540032.0, x7 = 3125.0 / 889945056.0;
+    const double x8 = (1549211.0 + 3246.0 * r) / 63063000.0;
+    const double z0 = 8887.0 / 4794.0, z1 = -1897.0 / 3196.0, z2 = 25259.0 / 575280.0;
+    const double z3 = -965093875.0 / 9674368704.0, z4 = -4093.0 / 4794.0;
+    const double z5 = 25698275.0 / 29023106112.0, z6 = -3907675.0 / 348277273344.0;
+    const double z7 = 11865625.0 / 3656911370112.0, z8 = 25.0 / 308756448.0;
+    P.push_back(Step{W(0), W(0), {out(W(1), 1.0, 0.0),                       // A4
+                                  out(W(2), x2, 0.0, {{W(0), x1}})}});       // x1 A2 + x2 A4
+    P.push_back(Step{W(1), W(2), {out(W(3), 1.0, 0.0),                                     // A8
+                                  out(W(4), 1.0, 0.0, {{W(1), x3}}),                       // x3 A4 + A8
+                                  out(W(5), x7, x4, {{W(0), x5}, {W(1), x6}}),             // x4 I + x5 A2 + x6 A4 + x7 A8
+                                  out(W(6), z3, z0, {{W(0), z1}, {W(1), z2}}),             // z0 I + z1 A2 + z2 A4 + z3 A8
+                                  out(W(7), z7, z5, {{W(0), z5}, {W(1), z6}})}});          // z5 I + z5 A2 + z6 A4 + z7 A8
+    P.push_back(Step{W(4), W(5), {out(SL_C, 1.0, 1.0, {{W(0), -0.5}, {W(1), x8}}),          // T16 = I - A2/2 + x8 A4 + A16
+                                  out(W(6), 0.0, 0.0, {{W(6), 1.0}}, {{0, z4}}),           // ... + z4 T16
+                                  out(W(7), 0.0, 0.0, {{W(7), 1.0}}, {{0, z8}})}});        // ... + z8 T16
+    P.push_back(Step{W(7), W(3), {out(W(2), 1.0, 0.0, {{W(6), 1.0}})}});                    // C24 = (...) A8; sum
+    P.push_back(Step{SL_A, W(2), {out(SL_S, as, 0.0)}});
+  } else {
+    // eq. Algorithm7cA with Coefs7cA, eq. Algorithm7sA with Coefs7sA.
+    // a[i][j-1] multiplies A_{2i} in C_j (A_0 = I).
+    static const double a[4][4] = {
+        {0.0, 0.55751443809990408029, 0.75936877868464999248, 0.0},
+        {0.0, -0.61577924683458386455, -0.01560333979813817129, -0.039649968743474473091},
+        {0.02264979811206039519, 0.00747198841446687051, 0.00010936989591908396,
+         0.000155490073503821463},
+        {-0.00013110924142135755, -0.00003362444420476012, -1.03893360877457159499e-6,
+         -1.126739663071170022488e-6}};
+    static const double z[12] = {0.10090808375109885598,   -0.07668753546445299316,
+                                 0.00084924846993243257,   -0.00001220406904464391,
+                                 0.98499703159318860027,   -0.84925233648155398756,
+                                 1.0,                      0.00095544138280925799,
+                                 4.56337109377154270633e-6, 2.73461259403000427141e-8,
+                                 0.00048550288474842477,   -4.15891109384923342531e-7};
+    P.push_back(Step{W(0), W(0), {out(W(1), 1.0, 0.0)}});  // A4
+    std::vector<OutSpec> o;
+    for (int j = 0; j < 4; ++j)  // C_{j+1} = a0 I + a1 A2 + a2 A4 + a3 A6 -> W2..W5
+      o.push_back(out(W(2 + j), a[3][j], a[0][j], {{W(0), a[1][j]}, {W(1), a[2][j]}}));
+    o.push_back(out(W(6), z[3], z[0], {{W(0), z[1]}, {W(1), z[2]}}));  // sine sum, first terms
+    o.push_back(out(W(7), z[9], z[6], {{W(0), z[7]}, {W(1), z[8]}}));  // left factor of C48
+    P.push_back(Step{W(1), W(0), o});                                  // A6 = A4 A2
+    P.push_back(Step{W(5), W(5), {out(W(4), 1.0, 0.0, {{W(4), 1.0}}),               // A12 = C3 + C4^2
+                                  out(W(3), 0.0, 0.0, {{W(3), 1.0}}, {{0, 1.0}}),    // C2 + A12
+                                  out(W(6), 0.0, 0.0, {{W(6), 1.0}}, {{0, z[4]}}),
+                                  out(W(7), 0.0, 0.0, {{W(7), 1.0}}, {{0, z[10]}})}});
+    P.push_back(Step{W(3), W(4), {out(SL_C, 1.0, 0.0, {{W(2), 1.0}}),               // T24 = C1 + A24
+                                  out(W(6), 0.0, 0.0, {{W(6), 1.0}}, {{0, z[5]}}),
+                                  out(W(7), 0.0, 0.0, {{W(7), 1.0}}, {{0, z[11]}})}});
+    P.push_back(Step{W(7), SL_C, {out(W(0), 1.0, 0.0, {{W(6), 1.0}})}});             // C48; sum
+    P.push_back(Step{SL_A, W(0), {out(SL_S, as, 0.0)}});
+  }
+  return P;
+}
+
+// -------------------------------------------------------------- execution ---
+namespace {
+
+struct F64Slots {
+  const double* p[SL_COUNT] = {};
+};
+
+template <typename T>
+Epilogue<T> build_epilogue(const Step& st, T* const* hi, T* const* lo) {
+  EpiBuilder<T> b;
+  std::vector<int> in_slots;
+  auto in_index = [&](int slot) {
+    for (size_t i = 0; i < in_slots.size(); ++i)
+      if (in_slots[i] == slot) return (int)i;
+    in_slots.push_back(slot);
+    return b.add_in(hi[slot], lo ? lo[slot] : nullptr);
+  };
+  for (const OutSpec& o : st.outs) {
+    const int t = b.add_out(hi[o.slot], o.alpha, o.gamma, lo ? lo[o.slot] : nullptr);
+    for (auto& bc : o.beta) b.beta(t, in_index(bc.first), bc.second);
+    for (auto& dc : o.delta) b.delta(t, dc.first, dc.second);
+  }
+  return b.e;
+}
+
+cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, const Layout& L, int m,
+                  int s, cudaStream_t stream) {
+  double* slot[SL_COUNT] = {};
+  double* ping[2] = {(double*)(ws + L.ping64[0]), (double*)(ws + L.ping64[1])};
+  const size_t n2 = (size_t)n * (size_t)n;
+  slot[SL_A] = const_cast<double*>(A);
+  slot[SL_C] = s == 0 ? C : ping[0];
+  slot[SL_S] = s == 0 ? S : ping[0] + n2;
+  for (int w = 0; w < kWorkSlots; ++w) slot[W(w)] = (double*)(ws + L.w[w]);
+  for (const Step& st : chain_plan(m, s)) {
+    Epilogue<double> e = build_epilogue<double>(st, slot, nullptr);
+    CS_CHECK(gemm_f64(slot[st.X], slot[st.Y], n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, stream));
+  }
+  // Double-angle steps (Sec. 1): [C'; S'] = [C; S] C, C' = 2X - I, S' = 2X.
+  for (int j = 0; j < s; ++j) {
+    double* cur = ping[j & 1];
+    const bool last = (j == s - 1);
+    double* nc = last ? C : ping[(j + 1) & 1];
+    double* ns = last ? S : ping[(j + 1) & 1] + n2;
+    Epilogue<double> e;
+    e.split_row = n;
+    e.n_out = 2;
+    e.out[0] = nc;
+    e.out[1] = ns;
+    e.alpha[0] = 2.0;
+    e.alpha[1] = 2.0;
+    e.gamma[0] = -1.0;
+    e.gamma[1] = 0.0;
+    CS_CHECK(gemm_f64(cur, cur, 2 * n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, stream));
+  }
+  return CS_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+size_t elem_size(cs_prec p) { return p == CS_FP32 ? sizeof(float) : sizeof(double); }
+
+cs_status check_prec(cs_prec prec) {
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32)
+    return fail(CS_EINVAL, "unknown precision");
+  return CS_OK;
+}
+
+thread_local double* t_pinned = nullptr;
+
+cs_status read_norm(const double* dev, double* host, cudaStream_t stream) {
+  if (!t_pinned) CS_CUDA_CHECK(cudaMallocHost((void**)&t_pinned, sizeof(double)));
+  CS_CUDA_CHECK(cudaMemcpyAsync(t_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CS_CUDA_CHECK(cudaStreamSynchronize(stream));
+  *host = *t_pinned;
+  return CS_OK;
+}
+
+}  // namespace
+
+cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* ws, const Layout& L,
+                   int m, int s, cudaStream_t stream);
+
+cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
+                      int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream) {
+  CS_CHECK(check_prec(prec));
+  if (n < 0 || n > kMaxN) return fail(CS_EINVAL, "n out of range [0, 65536]");
+  if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");
+  if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 16 or 24");
+  if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_s must be in [0, 64]");
+  const int table = prec == CS_FP64 ? 0 : 1;
+  if (n == 0) {
+    if (info) *info = cs_info{0.0, force_m == -1 ? 4 : force_m, force_s == -1 ? 0 : force_s, 0, table, 0.0};
+    return CS_OK;
+  }
+  if (!A || !C || !S) return fail(CS_EINVAL, "null matrix pointer");
+  const size_t bytes = (size_t)n * (size_t)n * elem_size(prec);
+  if (overlaps(A, bytes, C, bytes) || overlaps(A, bytes, S, bytes) || overlaps(C, bytes, S, bytes))
+    return fail(CS_EINVAL, "A, C and S must not overlap");
+  const Layout L = make_layout(n, prec);
+  if (!ws || ws_bytes < L.total) return fail(CS_EINVAL, "workspace missing or too small");
+  if (((uintptr_t)ws & 255) != 0) return fail(CS_EINVAL, "workspace must be 256-byte aligned");
+  char* w = (char*)ws;
+  double* nrm_dev = (double*)(w + L.norm_out);
+  if (prec == CS_FP32)
+    CS_CHECK(norm1_f32((const float*)A, n, (double*)(w + L.norm_partial), nrm_dev, stream));
+  else
+    CS_CHECK(norm1_f64((const double*)A, n, (double*)(w + L.norm_partial), nrm_dev, stream));
+  double nrm = 0.0;
+  CS_CHECK(read_norm(nrm_dev, &nrm, stream));
+  if (!isfinite(nrm)) return fail(CS_ENONFINITE, "||A||_1 is not finite");
+  int m, s;
+  if (force_m == -1) {
+    CS_CHECK(select_ms(nrm, table, &m, &s));
+  } else {
+    m = force_m;
+    s = force_s;
+  }
+  const int prods = products_of(m) + 2 * s;
+  if (info) *info = cs_info{nrm, m, s, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
+  if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, m, s, stream);
+  return run_tf32(A, n, prec, C, S, w, L, m, s, stream);
+}
+
+}  // namespace cs
+
+// ====================================================================== ABI ===
+extern "C" {
+
+cs_status cossin_workspace_size(int64_t n, cs_prec prec, size_t* bytes) {
+  if (!bytes) return cs::fail(CS_EINVAL, "bytes is null");
+  CS_CHECK(cs::check_prec(prec));
+  if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  *bytes = cs::make_layout(n, prec).total;
+  return CS_OK;
+}
+
+cs_status cossin_norm1(const void* A, int64_t n, cs_prec prec, double* norm1, cossin_stream_t stream) {
+  CS_CHECK(cs::check_prec(prec));
+  if (!norm1) return cs::fail(CS_EINVAL, "norm1 is null");
+  if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (n == 0) {
+    *norm1 = 0.0;
+    return CS_OK;
+  }
+  if (!A) return cs::fail(CS_EINVAL, "null matrix pointer");
+  const size_t part = sizeof(double) * ((size_t)cs::norm1_scratch_elems(n) + 1);
+  void* buf = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  CS_CUDA_CHECK(cudaMallocAsync(&buf, part, st));
+  double* out = (double*)buf;
+  double* partial = out + 1;
+  cs_status rc = prec == CS_FP32 ? cs::norm1_f32((const float*)A, n, partial, out, st)
+                                 : cs::norm1_f64((const double*)A, n, partial, out, st);
+  if (rc == CS_OK) rc = cs::read_norm(out, norm1, st);
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
+cs_status cossin_select(double norm1, int32_t table, int32_t* m, int32_t* s) {
+  if (!m || !s) return cs::fail(CS_EINVAL, "null output pointer");
+  int mm, ss;
+  CS_CHECK(cs::select_ms(norm1, table, &mm, &ss));
+  *m = mm;
+  *s = ss;
+  return CS_OK;
+}
+
+cs_status cossin_ex(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
+                    int32_t force_m, int32_t force_s, cs_info* info, cossin_stream_t stream) {
+  return cs::cossin_impl(A, n, prec, C, S, ws, ws_bytes, force_m, force_s, info, (cudaStream_t)stream);
+}
+
+cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossin_stream_t stream) {
+  CS_CHECK(cs::check_prec(prec));
+  if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (n == 0) return CS_OK;
+  size_t bytes = cs::make_layout(n, prec).total;
+  void* ws = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMallocAsync(&ws, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cs::fail(CS_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  cs_status rc = cs::cossin_impl(A, n, prec, C, S, ws, bytes, -1, -1, nullptr, st);
+  cudaFreeAsync(ws, st);
+  return rc;
+}
+
+const char* cossin_last_error(void) { return cs::g_last_error.c_str(); }
+
+void cossin_prof_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(cs::g_prof_mu);
+  cs::g_prof_on = on != 0;
+}
+
+void cossin_prof_reset(void) {
+  cs::prof_drain();
+  std::lock_guard<std::mutex> lk(cs::g_prof_mu);
+  for (int k = 0; k < CS_KERNEL_KINDS; ++k) {
+    cs::g_prof_ms[k] = 0;
+    cs::g_prof_n[k] = 0;
+    cs::g_prof_work[k] = 0;
+  }
+}
+
+cs_status cossin_prof_read(int32_t kind, double* ms, int64_t* launches, double* work) {
+  if (kind < 0 || kind >= CS_KERNEL_KINDS) return cs::fail(CS_EINVAL, "unknown kernel kind");
+  cs::prof_drain();
+  std::lock_guard<std::mutex> lk(cs::g_prof_mu);
+  if (ms) *ms = cs::g_prof_ms[kind];
+  if (launches) *launches = cs::g_prof_n[kind];
+  if (work) *work = cs::g_prof_work[kind];
+  return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// internal.cuh -- shared declarations of the cos/sin library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "cossin.h"
+
+namespace cs {
+
+// ---------------------------------------------------------------- errors ---
+void set_error(const std::string& msg);
+cs_status fail(cs_status st, const std::string& msg);
+cs_status cuda_fail(cudaError_t e, const char* what);
+
+#define CS_CUDA_CHECK(expr)                                   \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return ::cs::cuda_fail(e_, #expr); \
+  } while (0)
+
+#define CS_CHECK(expr)                       \
+  do {                                       \
+    cs_status st_ = (expr);                  \
+    if (st_ != CS_OK) return st_;            \
+  } while (0)
+
+// --------------------------------------------------------------- epilogue ---
+// Every product P = X Y of the method is followed by linear combinations of P,
+// the identity and matrices already computed (Sec. 2.1).  The epilogue applies
+// them where P leaves the accumulators:
+//   out_t[r][c] = alpha_t * P[r][c] + gamma_t * (r == c) + sum_j beta_tj * in_j[r][c]
+//                 + sum_{u < t} delta_tu * out_u[r][c]
+// In "stacked" mode (double-angle step, [C; S] * C) rows r < split_row go to
+// out_0 and rows r >= split_row go to out_1 at row r - split_row, each with its
+// own alpha and gamma, and no inputs are read.
+// out_t may equal in_j: each element is read before it is written, by the
+// same thread.
+constexpr int EPI_MAX_IN = 6;
+constexpr int EPI_MAX_OUT = 6;
+
+template <typename T>
+struct Epilogue {
+  int32_t n_in = 0;
+  int32_t n_out = 0;
+  int64_t split_row = -1;  // >= 0 selects stacked mode
+  const T* in[EPI_MAX_IN] = {};
+  T* out[EPI_MAX_OUT] = {};
+  // TF32 path: a matrix is held as a pair (hi, lo) with hi = tf32(x) and
+  // lo = x - hi exactly.  If out_lo[t] is non-null, out[t] receives hi and
+  // out_lo[t] receives lo; if in_lo[j] is non-null the input is in[j] + in_lo[j].
+  T* out_lo[EPI_MAX_OUT] = {};
+  const T* in_lo[EPI_MAX_IN] = {};
+  double alpha[EPI_MAX_OUT] = {};
+  double gamma[EPI_MAX_OUT] = {};
+  double beta[EPI_MAX_OUT][EPI_MAX_IN] = {};
+  double delta[EPI_MAX_OUT][EPI_MAX_OUT] = {};
+};
+
+template <typename T>
+struct EpiBuilder {
+  Epilogue<T> e;
+  int add_in(const T* p, const T* lo = nullptr) {
+    e.in[e.n_in] = p;
+    e.in_lo[e.n_in] = lo;
+    return e.n_in++;
+  }
+  int add_out(T* p, double alpha, double gamma, T* lo = nullptr) {
+    e.out[e.n_out] = p;
+    e.out_lo[e.n_out] = lo;
+    e.alpha[e.n_out] = alpha;
+    e.gamma[e.n_out] = gamma;
+    return e.n_out++;
+  }
+  void beta(int out, int in, double b) { e.beta[out][in] = b; }
+  void delta(int out, int prev_out, double d) { e.delta[out][prev_out] = d; }
+};
+
+// ------------------------------------------------------------- profiling ---
+struct ProfScope {
+  int kind;
+  double work;
+  cudaStream_t stream;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ProfScope(int kind, double work, cudaStream_t stream);
+  ~ProfScope();
+};
+
+// ---------------------------------------------------------------- kernels ---
+// FP64 product with fused epilogue: P = op(X) op(Y), op = identity or
+// transpose, M x N result, inner dimension K.  Batched over `batch` matrices
+// with element strides bsx, bsy (operands) and bse (every epilogue matrix).
+// ldo is the leading dimension of the epilogue matrices.
+cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
+                   int64_t ldx, int64_t ldy, bool transX, bool transY, const Epilogue<double>& epi,
+                   int64_t ldo, int64_t batch, int64_t bsx, int64_t bsy, int64_t bse,
+                   cudaStream_t stream);
+
+// ||A||_1 for an FP64 or FP32 matrix into a device double (*out_dev).
+// partial_dev: ceil(n / 8192)... scratch of norm1_scratch_elems(n) doubles.
+int64_t norm1_scratch_elems(int64_t n);
+cs_status norm1_f64(const double* A, int64_t n, double* partial_dev, double* out_dev,
+                    cudaStream_t stream);
+cs_status norm1_f32(const float* A, int64_t n, double* partial_dev, double* out_dev,
+                    cudaStream_t stream);
+
+// Host selection (step 2).
+cs_status select_ms(double norm1, int table, int* m, int* s);
+int products_of(int m);
+
+}  // namespace cs

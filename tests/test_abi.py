@@ -1,0 +1,97 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function declared in include/*.h; host-only calls behave as documented."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_00465_gb300 import _lib, api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert "cossin" in names and "cossin_ex" in names and len(names) >= 9
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_signatures_cover_header(L):
+    for name in declared_functions():
+        assert name in _lib.SIGNATURES, name
+
+
+def test_workspace_size_host_only(L):
+    assert api.workspace_size(0, "fp64") > 0
+    w64 = api.workspace_size(64, "fp64")
+    assert w64 >= 12 * 64 * 64 * 8
+    assert api.workspace_size(4096, "fp32") >= 24 * 4096 * 4096 * 4
+    with pytest.raises(_lib.CossinError) as e:
+        api.workspace_size(-1, "fp64")
+    assert e.value.status == _lib.CS_EINVAL
+    with pytest.raises(_lib.CossinError):
+        api.workspace_size(1 << 20, "fp64")
+
+
+@pytest.mark.parametrize("table,prec", [(0, "double"), (1, "single")])
+def test_select_matches_oracle(L, table, prec):
+    for nrm in np.concatenate([[0.0], np.geomspace(1e-8, 1e12, 800)]):
+        assert api.select(float(nrm), table) == oracle.select(float(nrm), prec), nrm
+
+
+def test_select_errors(L):
+    for bad, st in ((float("inf"), _lib.CS_ENONFINITE), (float("nan"), _lib.CS_ENONFINITE),
+                    (1e300, _lib.CS_ERANGE), (-1.0, _lib.CS_EINVAL)):
+        with pytest.raises(_lib.CossinError) as e:
+            api.select(bad, 0)
+        assert e.value.status == st
+    with pytest.raises(_lib.CossinError):
+        api.select(1.0, 2)
+
+
+def test_argument_errors_before_any_gpu_work(L):
+    """Checks that fail before the library touches the device."""
+    f = L.cossin_ex
+    info = _lib.CsInfo()
+    nul = ctypes.c_void_p(0)
+    assert f(nul, -1, 0, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert f(nul, 4, 7, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert f(nul, 4, 0, nul, nul, nul, 0, 24, -1, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert f(nul, 4, 0, nul, nul, nul, 0, 12, 0, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert f(nul, 4, 0, nul, nul, nul, 0, 24, 65, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert f(nul, 4, 0, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_EINVAL  # null A
+    a = ctypes.c_void_p(4096)
+    assert f(a, 4, 0, a, ctypes.c_void_p(8192), nul, 0, -1, -1, None, nul) == _lib.CS_EINVAL  # alias
+    assert b"overlap" in L.cossin_last_error()
+    # n = 0 is a no-op
+    assert f(nul, 0, 0, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_OK
+
+
+def test_library_has_no_cpu_fallback_symbols(L):
+    """The product path has no host implementation of the method to fall back on."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    assert "oracle" not in out
