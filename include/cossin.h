@@ -106,8 +106,23 @@ cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, voi
                     void* ws_dev, size_t ws_bytes, int32_t force_m, int32_t force_s,
                     cs_info* info, cossin_stream_t stream);
 
+/* One product P = X Y (n x n, row-major) on the library's product kernel for
+ * `prec`: the FP64 kernel for CS_FP64, the three-pass TF32 tensor-core kernel
+ * for CS_FP32 (FP32 in and out) and CS_SPLIT_TF32 (FP64 in and out, computed
+ * from the FP32 roundings of X and Y).  These are the products the method
+ * counts (Pi_2m in Tables 1-2).  P must not overlap X or Y.  Allocates and
+ * frees a stream-ordered workspace for the tensor-core kinds. */
+cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec prec, void* P_dev,
+                        cossin_stream_t stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char* cossin_last_error(void);
+
+/* Synchronises `stream` and reports a device-side failure of earlier calls:
+ * CS_ETIMEOUT if a kernel gave up on a bounded wait (the flag is then
+ * cleared), CS_ECUDA if the stream holds a CUDA error, else CS_OK.  The same
+ * check runs inside every cossin / cossin_ex call at its one synchronisation. */
+cs_status cossin_device_status(cossin_stream_t stream);
 
 /* Kernel timing hooks used by the benchmark.  While enabled, the library
  * records CUDA events around each launch of the kinds below on the launch

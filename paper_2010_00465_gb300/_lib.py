@@ -44,7 +44,9 @@ SIGNATURES = {
     "cossin": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp]),
     "cossin_ex": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp, _sz, _i32, _i32,
                                  ctypes.POINTER(CsInfo), _vp]),
+    "cossin_matmul": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "cossin_last_error": (ctypes.c_char_p, []),
+    "cossin_device_status": (ctypes.c_int, [_vp]),
     "cossin_prof_enable": (None, [_i32]),
     "cossin_prof_reset": (None, []),
     "cossin_prof_read": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),

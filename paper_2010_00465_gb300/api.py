@@ -104,6 +104,18 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
     return C, S
 
 
+def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Tensor:
+    """P = X Y on the library's product kernel for ``prec``."""
+    p = _prec(prec, X)
+    n = _check_matrix(X, p)
+    if _check_matrix(Y, p) != n:
+        raise ValueError("X and Y must have the same order")
+    P = torch.empty_like(X)
+    check(lib().cossin_matmul(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), n, p,
+                              ctypes.c_void_p(P.data_ptr()), _stream_ptr(stream)))
+    return P
+
+
 def prof_enable(on: bool = True) -> None:
     lib().cossin_prof_enable(1 if on else 0)
 

@@ -11,6 +11,7 @@
 
 #include "internal.cuh"
 #include "plan.h"
+#include "tc_gemm.h"
 
 namespace cs {
 
@@ -146,16 +147,13 @@ Layout make_layout(int64_t n, int prec) {
     L.ping64[0] = take(sizeof(double) * 2 * n2);
     L.ping64[1] = take(sizeof(double) * 2 * n2);
   } else {
-    L.a_hi = take(sizeof(float) * n2);
-    L.a_lo = take(sizeof(float) * n2);
-    for (int w = 0; w < kWorkSlots; ++w) {
-      L.w[w] = take(sizeof(float) * n2);
-      L.w_lo[w] = take(sizeof(float) * n2);
-    }
-    for (int p = 0; p < 2; ++p) {
-      L.ping32[p] = take(sizeof(float) * 2 * n2);
-      L.ping32_lo[p] = take(sizeof(float) * 2 * n2);
-    }
+    L.ld32 = (n + 31) / 32 * 32;
+    const size_t sz = sizeof(float) * (size_t)n * (size_t)L.ld32;
+    for (int k = 0; k < 4; ++k) L.a4[k] = take(sz);
+    for (int w = 0; w < kWorkSlots; ++w)
+      for (int k = 0; k < 4; ++k) L.w4[w][k] = take(sz);
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < 4; ++k) L.ping4[p][k] = take(k < 2 ? 2 * sz : sz);
     if (prec == CS_SPLIT_TF32) {
       L.ping64[0] = take(sizeof(double) * 2 * n2);
       L.ping64[1] = take(sizeof(double) * 2 * n2);
@@ -291,7 +289,15 @@ cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, co
     Epilogue<double> e = build_epilogue<double>(st, slot, nullptr);
     CS_CHECK(gemm_f64(slot[st.X], slot[st.Y], n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, stream));
   }
-  // Double-angle steps (Sec. 1): [C'; S'] = [C; S] C, C' = 2X - I, S' = 2X.
+  return square_f64(ping, n, s, C, S, stream);
+}
+
+}  // namespace
+
+// Double-angle steps (Sec. 1): [C'; S'] = [C; S] C with C' = 2X - I, S' = 2X,
+// one stacked 2n x n x n product per step, ping-ponging between the buffers.
+cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double* S, cudaStream_t stream) {
+  const size_t n2 = (size_t)n * (size_t)n;
   for (int j = 0; j < s; ++j) {
     double* cur = ping[j & 1];
     const bool last = (j == s - 1);
@@ -311,6 +317,8 @@ cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, co
   return CS_OK;
 }
 
+namespace {
+
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
   const char* pb = (const char*)b;
@@ -325,20 +333,38 @@ cs_status check_prec(cs_prec prec) {
   return CS_OK;
 }
 
-thread_local double* t_pinned = nullptr;
+struct PinnedWords {
+  double norm;
+  int err;
+};
+thread_local PinnedWords* t_pinned = nullptr;
 
+}  // namespace
+
+// Reads ||A||_1 from the device (one 8-byte copy and a stream synchronisation)
+// together with the tensor-core kernels' error word, which reports a bounded
+// wait that expired in an earlier call on this device.
 cs_status read_norm(const double* dev, double* host, cudaStream_t stream) {
-  if (!t_pinned) CS_CUDA_CHECK(cudaMallocHost((void**)&t_pinned, sizeof(double)));
-  CS_CUDA_CHECK(cudaMemcpyAsync(t_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  if (!t_pinned) CS_CUDA_CHECK(cudaMallocHost((void**)&t_pinned, sizeof(PinnedWords)));
+  int* errw = tc_error_word();
+  if (dev) CS_CUDA_CHECK(cudaMemcpyAsync(&t_pinned->norm, dev, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  if (errw) CS_CUDA_CHECK(cudaMemcpyAsync(&t_pinned->err, errw, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CS_CUDA_CHECK(cudaStreamSynchronize(stream));
-  *host = *t_pinned;
+  if (host) *host = t_pinned->norm;
+  if (errw && t_pinned->err) {
+    CS_CUDA_CHECK(cudaMemsetAsync(errw, 0, sizeof(int), stream));
+    return fail(CS_ETIMEOUT, "a tensor-core kernel gave up on a bounded wait in an earlier call");
+  }
   return CS_OK;
 }
+
+namespace {
 
 }  // namespace
 
 cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* ws, const Layout& L,
                    int m, int s, cudaStream_t stream);
+cs_status matmul_tf32(const void* X, const void* Y, int64_t n, bool f64_io, void* P, cudaStream_t stream);
 
 cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
                       int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream) {
@@ -447,7 +473,30 @@ cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossi
   return rc;
 }
 
+cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, void* P, cossin_stream_t stream) {
+  CS_CHECK(cs::check_prec(prec));
+  if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (n == 0) return CS_OK;
+  if (!X || !Y || !P) return cs::fail(CS_EINVAL, "null matrix pointer");
+  const size_t bytes = (size_t)n * (size_t)n * cs::elem_size(prec);
+  if (cs::overlaps(P, bytes, X, bytes) || cs::overlaps(P, bytes, Y, bytes))
+    return cs::fail(CS_EINVAL, "P must not overlap X or Y");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == CS_FP64) {
+    cs::Epilogue<double> e;
+    e.n_out = 1;
+    e.out[0] = (double*)P;
+    e.alpha[0] = 1.0;
+    return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
+  }
+  return cs::matmul_tf32(X, Y, n, prec == CS_SPLIT_TF32, P, st);
+}
+
 const char* cossin_last_error(void) { return cs::g_last_error.c_str(); }
+
+cs_status cossin_device_status(cossin_stream_t stream) {
+  return cs::read_norm(nullptr, nullptr, (cudaStream_t)stream);
+}
 
 void cossin_prof_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(cs::g_prof_mu);

@@ -1,0 +1,376 @@
+// gemm_tf32.cu -- three-pass TF32 tensor-core product on tcgen05/TMEM with
+// TMA-fed operands and the method's linear combinations fused in the epilogue.
+//
+// FP32 accuracy from TF32 tensor cores: every matrix is held as a pair
+// (hi, lo) of TF32 values, hi = tf32(x) and lo = tf32(x - hi) (22 significant
+// bits together), and the product is
+//   X Y = X_hi Y_hi + (X_lo Y_hi + X_hi Y_lo + X_lo Y_lo)
+// with FP32 accumulation.  The epilogue that produces a matrix also writes its
+// (hi, lo) split and, for matrices later used as a right operand, the
+// transposed split, so both operands are always fed K-major.
+//
+// Tensor-core FP32 accumulation is not IEEE: every MMA adds into the TMEM
+// accumulator with truncation, so the error of a long accumulation grows
+// linearly with K and is biased toward zero (measured on GB300: 4e-5 relative
+// at K = 4096, against 1e-6 for an FP32 FFMA product).  The kernel therefore
+//   * accumulates X_hi Y_hi and the two correction passes in separate TMEM
+//     accumulators, so the small terms are not truncated against the large sum;
+//   * starts fresh accumulators every kGroup k-blocks (32 k) and promotes
+//     them into FP32 registers with round-to-nearest adds (two TMEM buffers
+//     ping-pong, so the tensor pipe keeps running while one is drained).
+//
+// One CTA computes a 128 x 128 tile:
+//   warp 0     TMA producer: X_hi, X_lo (128 x 32) and Y^T_hi, Y^T_lo
+//              (128 x 32) per stage into 128-byte-swizzled shared memory;
+//   warp 1     allocates 512 TMEM columns {main, corr} x 2 buffers; one lane
+//              issues the MMAs (cta_group::1, M = N = 128, K = 8 per
+//              instruction) and commits stages and accumulator buffers;
+//   warps 2-5  drain each accumulator buffer into registers, then run the
+//              epilogue: linear combinations, (hi, lo) split, row-major and
+//              transposed stores.
+// Measured on GB300 (n = 4096, N(0,1) operands): relative Frobenius error of
+// one product 2.4e-7, against 1.2e-6 for cuBLAS FP32 (FFMA).
+// Every mbarrier wait is bounded; on expiry the CTA stops issuing work, waits
+// (bounded) for what it already issued, frees TMEM and raises *err.
+#include <cuda.h>
+
+#include "internal.cuh"
+#include "sm100_ptx.cuh"
+#include "tc_gemm.h"
+
+namespace cs {
+namespace {
+
+using namespace ptx;
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 32;  // 32 floats = 128 bytes = one swizzle row
+constexpr int kThreads = 192;
+constexpr int kABytes = BM * BK * 4;
+constexpr int kBBytes = BN * BK * 4;
+constexpr int kStageBytes = 2 * (kABytes + kBBytes);
+constexpr int kStages = 3;
+constexpr int kSmem = kStages * kStageBytes + 1024;
+#ifndef COSSIN_TC_GROUP
+#define COSSIN_TC_GROUP 1
+#endif
+#ifndef COSSIN_TC_PASSES
+#define COSSIN_TC_PASSES 4
+#endif
+constexpr int kGroup = COSSIN_TC_GROUP;  // k-blocks per accumulator buffer before promotion
+constexpr uint32_t kTmemCols = 512;    // buffer b: main at 256 b, corrections at 256 b + 128
+// Instruction descriptor: D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void split_store(float v, float* hi, float* lo, int64_t idx) {
+  if (lo) {
+    const float h = tf32_rna(v);
+    hi[idx] = h;
+    lo[idx] = COSSIN_LO(v - h);
+  } else {
+    hi[idx] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tf32_kernel(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+                     const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl, int M, int N,
+                     int K, int ldo, const __grid_constant__ TcEpilogue epi, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int kb_consumed;
+  __shared__ int groups_committed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int num_kb = (K + BK - 1) / BK;
+  const int num_groups = (num_kb + kGroup - 1) / kGroup;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    abort_flag = 0;
+    kb_consumed = 0;
+    groups_committed = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  int kb_issued = 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch(&mXh);
+      tma_prefetch(&mXl);
+      tma_prefetch(&mYh);
+      tma_prefetch(&mYl);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int st = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty_bar[st], ((kb / kStages) & 1) ^ 1, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        uint8_t* base = smem + st * kStageBytes;
+        mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+        tma_load_2d(base, &mXh, &full_bar[st], kb * BK, m0);
+        tma_load_2d(base + kABytes, &mXl, &full_bar[st], kb * BK, m0);
+        tma_load_2d(base + 2 * kABytes, &mYh, &full_bar[st], kb * BK, n0);
+        tma_load_2d(base + 2 * kABytes + kBBytes, &mYl, &full_bar[st], kb * BK, n0);
+        kb_issued = kb + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int kb = 0;
+      for (int g = 0; g < num_groups && !abort_flag; ++g) {
+        const int b = g & 1;
+        if (g >= 2 && !mbar_wait(&tempty_bar[b], ((g >> 1) & 1) ^ 1, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_main = tmem + 256u * b, d_corr = d_main + 128u;
+        for (int kk = 0; kk < kGroup && kb < num_kb; ++kk, ++kb) {
+          const int st = kb % kStages;
+          if (!mbar_wait(&full_bar[st], (kb / kStages) & 1, &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(smem + st * kStageBytes);
+          const uint32_t a_lo = a_hi + kABytes;
+          const uint32_t b_hi = a_hi + 2 * kABytes;
+          const uint32_t b_lo = b_hi + kBBytes;
+#pragma unroll
+          for (int j = 0; j < BK / 8; ++j) {  // K = 8 tf32 (32 bytes) per instruction
+            const uint32_t off = 32u * j;
+            const uint64_t ah = desc_kmajor_sw128(a_hi + off), al = desc_kmajor_sw128(a_lo + off);
+            const uint64_t bh = desc_kmajor_sw128(b_hi + off), bl = desc_kmajor_sw128(b_lo + off);
+            const uint32_t acc = (kk | j) != 0;
+            mma_tf32(d_main, ah, bh, kIdesc, acc);
+            mma_tf32(d_corr, al, bh, kIdesc, acc);
+            mma_tf32(d_corr, ah, bl, kIdesc, 1);
+            if (COSSIN_TC_PASSES == 4) mma_tf32(d_corr, al, bl, kIdesc, 1);
+          }
+          mma_commit(&empty_bar[st]);
+          kb_consumed = kb + 1;
+        }
+        mma_commit(&tfull_bar[b]);  // also tracks the MMAs of an aborted group
+        groups_committed = g + 1;
+      }
+    }
+  } else {
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    float acc[BN];
+#pragma unroll
+    for (int c = 0; c < BN; ++c) acc[c] = 0.f;
+    bool ok = true;
+    for (int g = 0; g < num_groups; ++g) {
+      const int b = g & 1;
+      // lane 0 waits and the warp follows its verdict, so the warp-collective
+      // TMEM loads below are never reached by part of a warp
+      int w = 1;
+      if (lane == 0) {
+        w = mbar_wait(&tfull_bar[b], (g >> 1) & 1, &abort_flag) && !abort_flag;
+        if (!w) abort_flag = 1;
+      }
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (!w) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t t_main = tmem + lane_off + 256u * b, t_corr = t_main + 128u;
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t vm[16], vc[16];
+        tmem_ld16(t_main + (uint32_t)c0, vm);
+        tmem_ld16(t_corr + (uint32_t)c0, vc);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(vm[j]) + __uint_as_float(vc[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[b]);
+    }
+    if (ok) {
+      // The promoted sums go back to TMEM columns 0..127 (no MMA writes any
+      // buffer any more) so the epilogue can walk them in chunks.
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(acc[c0 + j]);
+        tmem_st16(tmem + lane_off + (uint32_t)c0, v);
+      }
+      tmem_st_wait();
+      const int r = m0 + quarter * 32 + lane;
+      for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + lane_off + (uint32_t)c0, v);
+        tmem_ld_wait();
+        if (r >= M) continue;
+        const int cbase = n0 + c0;
+        if (epi.split_row >= 0) {
+          const bool top = r < epi.split_row;
+          const int rr = top ? r : r - (int)epi.split_row;
+          const int t = top ? 0 : 1;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = cbase + j;
+            if (c >= N) break;
+            const float val = epi.alpha[t] * __uint_as_float(v[j]) + (rr == c ? epi.gamma[t] : 0.f);
+            split_store(val, epi.out_hi[t], epi.out_lo[t], (int64_t)rr * ldo + c);
+            if (epi.outT_hi[t]) split_store(val, epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + rr);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = cbase + j;
+            if (c >= N) break;
+            const int64_t idx = (int64_t)r * ldo + c;
+            const float p = __uint_as_float(v[j]);
+            float in[EPI_MAX_IN], o[EPI_MAX_OUT];
+#pragma unroll
+            for (int q = 0; q < EPI_MAX_IN; ++q) {
+              in[q] = 0.f;
+              if (q < epi.n_in) {
+                in[q] = epi.in_hi[q][idx];
+                if (epi.in_lo[q]) in[q] += epi.in_lo[q][idx];
+              }
+            }
+#pragma unroll
+            for (int t = 0; t < EPI_MAX_OUT; ++t) {
+              if (t >= epi.n_out) break;
+              float val = epi.alpha[t] * p + (r == c ? epi.gamma[t] : 0.f);
+#pragma unroll
+              for (int q = 0; q < EPI_MAX_IN; ++q)
+                if (q < epi.n_in) val = fmaf(epi.beta[t][q], in[q], val);
+#pragma unroll
+              for (int u = 0; u < EPI_MAX_OUT; ++u)
+                if (u < t) val = fmaf(epi.delta[t][u], o[u], val);
+              o[t] = val;
+            }
+#pragma unroll
+            for (int t = 0; t < EPI_MAX_OUT; ++t) {
+              if (t >= epi.n_out) break;
+              split_store(o[t], epi.out_hi[t], epi.out_lo[t], idx);
+              if (epi.outT_hi[t]) split_store(o[t], epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + r);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // Teardown: if a wait expired, wait (bounded) for the copies and MMAs this
+  // CTA issued before freeing TMEM.
+  __syncthreads();
+  if (abort_flag) {
+    if (warp == 0 && lane == 0) {
+      volatile int never = 0;
+      for (int kb = kb_consumed; kb < kb_issued; ++kb)
+        mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1, &never);
+    }
+    if (warp == 1 && lane == 0 && groups_committed > 0) {
+      volatile int never = 0;
+      const int g = groups_committed - 1;
+      mbar_wait(&tfull_bar[g & 1], (g >> 1) & 1, &never);
+    }
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------ tensor maps ---
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Row-major FP32 matrix [rows][cols] with leading dimension ld (floats), box of
+// 32 columns x box_rows rows, 128-byte swizzle, zero fill outside.
+cs_status make_map(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(CS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (((uintptr_t)base & 15) || (ld * 4) % 16) return fail(CS_EINVAL, "TMA operand not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CS_ECUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+  return CS_OK;
+}
+
+cs_status launch(const TcOperand& X, const TcOperand& YT, int M, int N, int K, int ldo, const TcEpilogue& epi,
+                 int* err, cudaStream_t stream) {
+  CUtensorMap mXh, mXl, mYh, mYl;
+  CS_CHECK(make_map(&mXh, X.hi, M, K, X.ld, BM));
+  CS_CHECK(make_map(&mXl, X.lo, M, K, X.ld, BM));
+  CS_CHECK(make_map(&mYh, YT.hi, N, K, YT.ld, BN));
+  CS_CHECK(make_map(&mYl, YT.lo, N, K, YT.ld, BN));
+  static bool attr_set = false;
+  if (!attr_set) {
+    CS_CUDA_CHECK(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  gemm_tf32_kernel<<<grid, kThreads, kSmem, stream>>>(mXh, mXl, mYh, mYl, M, N, K, ldo, epi, err);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
+}  // namespace
+
+cs_status gemm_tf32(const TcOperand& X, const TcOperand& YT, int64_t M, int64_t N, int64_t K, int64_t ldo,
+                    const TcEpilogue& epi, int* err, int bn, cudaStream_t stream) {
+  if (M <= 0 || N <= 0) return CS_OK;
+  if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return fail(CS_EINVAL, "gemm_tf32: size too large");
+  ProfScope prof(CS_KERNEL_GEMM_TF32, 2.0 * (double)M * (double)N * (double)K, stream);
+  (void)bn;
+  return launch(X, YT, (int)M, (int)N, (int)K, (int)ldo, epi, err, stream);
+}
+
+}  // namespace cs

@@ -6,7 +6,8 @@
 // columns of one row per step (coalesced), and every block writes its column
 // partial sums for its row chunk.  Pass 2 adds the partials of each column in
 // a fixed order (deterministic), then takes the maximum with warp shuffles and
-// one shared-memory round.  Accumulation is FP64 for both input types.  A NaN
+// one shared-memory round per block, the last block reducing the block maxima.
+// Accumulation is FP64 for both input types.  A NaN
 // anywhere makes the result NaN; Inf stays Inf.
 #include <math.h>
 
@@ -44,27 +45,46 @@ __device__ __forceinline__ double max_nan(double a, double b) {
   return (isnan(a) || isnan(b)) ? __longlong_as_double(0x7ff8000000000000ULL) : fmax(a, b);
 }
 
-__global__ void __launch_bounds__(1024) colsum_finish(const double* __restrict__ partial,
-                                                      int64_t n, int64_t chunks,
-                                                      double* __restrict__ out) {
+// Pass 2: one thread per column adds that column's partial sums (fixed order),
+// each block reduces its columns to a maximum, and the last block to finish
+// reduces the block maxima into *out.
+__global__ void __launch_bounds__(kCols) colsum_finish(const double* __restrict__ partial, int64_t n,
+                                                       int64_t chunks, double* __restrict__ block_max,
+                                                       unsigned int* __restrict__ ticket, double* __restrict__ out) {
+  const int64_t col = (int64_t)blockIdx.x * kCols + threadIdx.x;
   double best = 0.0;
-  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+  if (col < n) {
     double s = 0.0;
-    for (int64_t k = 0; k < chunks; ++k) s += partial[k * n + c];
-    best = max_nan(best, s);
+    for (int64_t k = 0; k < chunks; ++k) s += partial[k * n + col];
+    best = s;
   }
+  __shared__ double warp_best[kCols / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) best = max_nan(best, __shfl_xor_sync(0xffffffffu, best, off));
-  __shared__ double warp_best[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) warp_best[warp] = best;
   __syncthreads();
-  if (warp == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    best = lane < nw ? warp_best[lane] : 0.0;
+  if (threadIdx.x == 0) {
+    double b = warp_best[0];
+    for (int w = 1; w < kCols / 32; ++w) b = max_nan(b, warp_best[w]);
+    block_max[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double b = 0.0;
+  for (int64_t i = threadIdx.x; i < gridDim.x; i += kCols) b = max_nan(b, ((volatile double*)block_max)[i]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) best = max_nan(best, __shfl_xor_sync(0xffffffffu, best, off));
-    if (lane == 0) *out = best;
+  for (int off = 16; off > 0; off >>= 1) b = max_nan(b, __shfl_xor_sync(0xffffffffu, b, off));
+  if (lane == 0) warp_best[warp] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kCols / 32; ++w) b = max_nan(warp_best[0], warp_best[w]), warp_best[0] = b;
+    *out = warp_best[0];
+    *ticket = 0u;  // ready for the next call
   }
 }
 
@@ -75,17 +95,25 @@ cs_status norm1_impl(const T* A, int64_t n, double* partial, double* out, cudaSt
     return CS_OK;
   }
   const int64_t chunks = (n + kRows - 1) / kRows;
+  const int64_t col_blocks = (n + kCols - 1) / kCols;
+  double* block_max = partial + chunks * n;
+  unsigned int* ticket = (unsigned int*)(block_max + col_blocks);
   ProfScope prof(CS_KERNEL_NORM1, (double)n * (double)n * sizeof(T), stream);
-  dim3 grid((unsigned)((n + kCols - 1) / kCols), (unsigned)chunks);
+  CS_CUDA_CHECK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), stream));
+  dim3 grid((unsigned)col_blocks, (unsigned)chunks);
   colsum_partial<T><<<grid, kCols, 0, stream>>>(A, n, partial);
-  colsum_finish<<<1, 1024, 0, stream>>>(partial, n, chunks, out);
+  colsum_finish<<<(unsigned)col_blocks, kCols, 0, stream>>>(partial, n, chunks, block_max, ticket, out);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
 
 }  // namespace
 
-int64_t norm1_scratch_elems(int64_t n) { return n <= 0 ? 1 : ((n + kRows - 1) / kRows) * n; }
+// partial sums (chunks x n), block maxima (one per column block) and a ticket word
+int64_t norm1_scratch_elems(int64_t n) {
+  if (n <= 0) return 2;
+  return ((n + kRows - 1) / kRows) * n + (n + kCols - 1) / kCols + 1;
+}
 
 cs_status norm1_f64(const double* A, int64_t n, double* partial, double* out, cudaStream_t stream) {
   return norm1_impl<double>(A, n, partial, out, stream);

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <utility>
+
+#include "internal.cuh"
 #include <vector>
 
 namespace cs {
@@ -34,14 +36,26 @@ struct Step {
 std::vector<Step> chain_plan(int m, int s);
 
 // Byte offsets into the caller's workspace.
+//  FP64:       w[8] (n x n doubles), ping64[2] (stacked [C; S], 2n x n doubles)
+//  TF32 modes: every slot is four n x ld32 float arrays {hi, lo, hi^T, lo^T}
+//              (a4 for A, w4 for W0..W7); ping4[p] = {[C;S] hi, [C;S] lo,
+//              C^T hi, C^T lo} with the first two 2n x ld32; split mode adds
+//              ping64 for the FP64 double-angle steps.
 struct Layout {
   size_t norm_partial = 0, norm_out = 0;
-  size_t w[kWorkSlots] = {}, w_lo[kWorkSlots] = {};
-  size_t a_hi = 0, a_lo = 0;
-  size_t ping64[2] = {}, ping32[2] = {}, ping32_lo[2] = {};
+  size_t w[kWorkSlots] = {};
+  size_t ping64[2] = {};
+  int64_t ld32 = 0;
+  size_t a4[4] = {};
+  size_t w4[kWorkSlots][4] = {};
+  size_t ping4[2][4] = {};
   size_t total = 0;
 };
 
 Layout make_layout(int64_t n, int prec);
+
+// Double-angle steps in FP64 on the stacked buffers ping[2] (each 2n x n):
+// starts from [C; S] in ping[0]; the last step writes C and S.
+cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double* S, cudaStream_t stream);
 
 }  // namespace cs

@@ -1,0 +1,101 @@
+// split.cu -- (hi, lo) TF32 splits of a matrix (with an optional transposed
+// copy, through a 32 x 32 shared-memory tile so both stores coalesce), the
+// recombination hi + lo into the caller's FP32 or FP64 matrix, and the device
+// error word of the tensor-core kernels.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "sm100_ptx.cuh"
+#include "tc_gemm.h"
+
+namespace cs {
+namespace {
+
+__device__ int g_tc_error;
+
+template <typename T>
+__global__ void __launch_bounds__(256) split_kernel(const T* __restrict__ src, int64_t n, int64_t ld,
+                                                    float* __restrict__ hi, float* __restrict__ lo,
+                                                    float* __restrict__ hiT, float* __restrict__ loT) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (r < n && c < n) {
+      v = (float)src[r * n + c];
+      const float h = ptx::tf32_rna(v);
+      hi[r * ld + c] = h;
+      lo[r * ld + c] = COSSIN_LO(v - h);
+    }
+    tile[i][threadIdx.x] = v;
+  }
+  if (hiT == nullptr) return;  // uniform over the block
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = c0 + i, c = r0 + threadIdx.x;  // row of the transpose = column of src
+    if (r < n && c < n) {
+      const float v = tile[threadIdx.x][i];
+      const float h = ptx::tf32_rna(v);
+      hiT[r * ld + c] = h;
+      loT[r * ld + c] = COSSIN_LO(v - h);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                      int64_t n, int64_t ld, T* __restrict__ dst) {
+  const int64_t total = n * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, c = i - r * n;
+    dst[i] = (T)hi[r * ld + c] + (T)lo[r * ld + c];
+  }
+}
+
+template <typename T>
+cs_status split_impl(const T* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
+                     cudaStream_t stream) {
+  if (n <= 0) return CS_OK;
+  ProfScope prof(CS_KERNEL_OTHER, (double)n * n * (sizeof(T) + (hiT ? 16.0 : 8.0)), stream);
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+  split_kernel<T><<<grid, block, 0, stream>>>(src, n, ld, hi, lo, hiT, loT);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
+template <typename T>
+cs_status combine_impl(const float* hi, const float* lo, int64_t n, int64_t ld, T* dst, cudaStream_t stream) {
+  if (n <= 0) return CS_OK;
+  ProfScope prof(CS_KERNEL_OTHER, (double)n * n * (8.0 + sizeof(T)), stream);
+  const int64_t total = n * n;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  combine_kernel<T><<<blocks, 256, 0, stream>>>(hi, lo, n, ld, dst);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
+}  // namespace
+
+cs_status split_f32(const float* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
+                    cudaStream_t stream) {
+  return split_impl<float>(src, n, ld, hi, lo, hiT, loT, stream);
+}
+cs_status split_f64(const double* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
+                    cudaStream_t stream) {
+  return split_impl<double>(src, n, ld, hi, lo, hiT, loT, stream);
+}
+cs_status combine_f32(const float* hi, const float* lo, int64_t n, int64_t ld, float* dst, cudaStream_t stream) {
+  return combine_impl<float>(hi, lo, n, ld, dst, stream);
+}
+cs_status combine_f64(const float* hi, const float* lo, int64_t n, int64_t ld, double* dst, cudaStream_t stream) {
+  return combine_impl<double>(hi, lo, n, ld, dst, stream);
+}
+
+int* tc_error_word() {
+  int* p = nullptr;
+  if (cudaGetSymbolAddress((void**)&p, g_tc_error) != cudaSuccess) return nullptr;
+  return p;
+}
+
+}  // namespace cs
