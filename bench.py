@@ -370,6 +370,22 @@ def extra_launches(prec, info):
     return 2  # splitting A and the final recombination
 
 
+def traffic_of(kernel):
+    """DRAM bytes per launch from the committed ncu summary, only while the
+    kernel source is unchanged since the capture (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha256_16"]:
+        return None
+    return rec["read_bytes"] + rec["write_bytes"]
+
+
 def roofline(kind, ms, launches, work, pk, pk_kind, clocks):
     """achieved = algorithmic flops per launch / average launch time (CUDA
     events around every launch on the launch stream, inside the timed region)."""
@@ -382,14 +398,14 @@ def roofline(kind, ms, launches, work, pk, pk_kind, clocks):
         mhz = clocks.get("sm_mhz") or 2070.0
         peak = 2 * 2 * 152 * mhz * 1e6 / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "gemm_f64_kernel",
+                "frac": achieved / peak, "traffic": traffic_of("gemm_f64_kernel"), "kernel": "gemm_f64_kernel",
                 "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x median SM clock under load (%.0f MHz)" % mhz}
     # TF32 tensor: half the bf16 rate (nominal 1.1 vs 2.25 PFLOP/s); four passes per product
     bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     peak = bf16 * 1100.0 / 2250.0
     issued = achieved * 4
     return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
-            "traffic": None, "kernel": "gemm_tf32_kernel",
+            "traffic": traffic_of("gemm_tf32_kernel"), "kernel": "gemm_tf32_kernel",
             "peak_note": "%s sustained bf16 x nominal tf32/bf16 ratio; achieved counts the 4 TF32 passes"
                          % pk_kind, "algorithmic_tflops": achieved}
 
