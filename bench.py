@@ -421,6 +421,12 @@ def accuracy(api, dev_in, outs, work):
     res["fp64_64x64_rel_err_vs_oracle"] = max(
         float(np.linalg.norm(C.cpu().numpy() - Co) / np.linalg.norm(Co)),
         float(np.linalg.norm(S.cpu().numpy() - So) / np.linalg.norm(So)))
+    ref = {(f, r): (C, S) for (p, f, r), (C, S) in zip(work, outs) if p == "fp64"}
+    for (p, f, r), (C, S) in zip(work, outs):
+        if p != "fp64" and (f, r) in ref:
+            C64, S64 = ref[(f, r)]
+            res["%s_vs_fp64_path_%s_norm%g" % (p, f, r)] = max(
+                float((C.double() - C64).norm() / C64.norm()), float((S.double() - S64).norm() / S64.norm()))
     for (p, f, r), Ad, (C, S) in zip(work, dev_in, outs):
         if f == "normal" and r == 64.0:
             Cd, Sd = C.double(), S.double()
