@@ -85,6 +85,26 @@ cs_status cossin_workspace_size(int64_t n, cs_prec prec, size_t* bytes);
 cs_status cossin_norm1(const void* A_dev, int64_t n, cs_prec prec, double* norm1,
                        cossin_stream_t stream);
 
+/* Step 1 for callers that cannot allocate device memory: code that runs while
+ * a CUDA graph is being captured (an allocation there breaks the capture),
+ * code inside a framework whose device memory must all come from the
+ * framework's own pool, and latency-sensitive loops where cudaMalloc's
+ * implicit synchronisation is not acceptable.  The paper has no counterpart;
+ * this is the same computation as cossin_norm1, but it allocates nothing and
+ * does not synchronise: theta = ||A||_1 is written to the device double
+ * *norm1_dev on `stream`.
+ *   - n must be <= 4096 (CS_EINVAL otherwise).  The scratch is a static
+ *     device array of about 2 MB that every GPU loading the library holds
+ *     until the process exits.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents (the words that must start at zero are cleared on
+ *     `stream` by each call).  Calls that overlap on the GPU (concurrent
+ *     streams, or concurrent host threads on one device) race: serialise them. */
+cs_status cossin_norm1_noalloc(const void* A_dev, int64_t n, cs_prec prec, double* norm1_dev,
+                               cossin_stream_t stream);
+
 /* Step 2 on the host: the (2m, s) of minimal cost Pi_2m + 2 s over the four
  * families with ||A_s||_1 = theta / 2^s <= min(theta^c_2m, theta^s_2m)
  * (Tables 1-2; ties go to the smaller s).  table: 0 double, 1 single. */

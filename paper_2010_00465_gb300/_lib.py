@@ -40,6 +40,7 @@ _sz = ctypes.c_size_t
 SIGNATURES = {
     "cossin_workspace_size": (ctypes.c_int, [_i64, ctypes.c_int, ctypes.POINTER(_sz)]),
     "cossin_norm1": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
+    "cossin_norm1_noalloc": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp]),
     "cossin_select": (ctypes.c_int, [ctypes.c_double, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "cossin": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp]),
     "cossin_ex": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp, _sz, _i32, _i32,

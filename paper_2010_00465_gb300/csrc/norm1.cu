@@ -11,6 +11,8 @@
 // anywhere makes the result NaN; Inf stays Inf.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace cs {
@@ -122,5 +124,56 @@ cs_status norm1_f64(const double* A, int64_t n, double* partial, double* out, cu
 cs_status norm1_f32(const float* A, int64_t n, double* partial, double* out, cudaStream_t stream) {
   return norm1_impl<float>(A, n, partial, out, stream);
 }
+
+// ------------------------------------------------- allocation-free variant ---
+// Scratch for callers that cannot allocate device memory: the partial sums,
+// block maxima and ticket word of the two passes above for n <= kStaticMaxN,
+// about 2 MB, held by every GPU that loads the library until the process ends.
+constexpr int64_t kStaticMaxN = 4096;
+constexpr int64_t kStaticElems = ((kStaticMaxN + kRows - 1) / kRows) * kStaticMaxN +
+                                 (kStaticMaxN + kCols - 1) / kCols + 1;
+static __device__ __align__(256) double g_static_scratch[kStaticElems];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_addr[kMaxDevices] = {};
+
+// The array's name in host code is only a host-side stand-in; its device
+// address is looked up once per device, with that device current.
+cs_status static_scratch(double** out) {
+  int dev = 0;
+  CS_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(CS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    double* p = nullptr;
+    CS_CUDA_CHECK(cudaGetSymbolAddress((void**)&p, g_static_scratch));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return CS_OK;
+}
+}  // namespace
+
+}  // namespace cs
+
+extern "C" cs_status cossin_norm1_noalloc(const void* A, int64_t n, cs_prec prec, double* norm1_dev,
+                                          cossin_stream_t stream) {
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32) return cs::fail(CS_EINVAL, "unknown precision");
+  if (n < 0) return cs::fail(CS_EINVAL, "n must be >= 0");
+  if (n > cs::kStaticMaxN)
+    return cs::fail(CS_EINVAL, "cossin_norm1_noalloc: n = " + std::to_string(n) +
+                                   " exceeds the static scratch limit of 4096; use cossin_norm1");
+  if (!norm1_dev) return cs::fail(CS_EINVAL, "norm1_dev is null");
+  if (n > 0 && !A) return cs::fail(CS_EINVAL, "null matrix pointer");
+  double* scratch = nullptr;
+  CS_CHECK(cs::static_scratch(&scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == CS_FP32) return cs::norm1_f32((const float*)A, n, scratch, norm1_dev, st);
+  return cs::norm1_f64((const double*)A, n, scratch, norm1_dev, st);
+}
+
+namespace cs {
 
 }  // namespace cs
