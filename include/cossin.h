@@ -135,6 +135,42 @@ cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, voi
 cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec prec, void* P_dev,
                         cossin_stream_t stream);
 
+/* ------------------------------------------------------------ batched ---
+ * cos and sin of `count` FP32 matrices of orders n[i] <= 256 (host array),
+ * each with its own theta, (2m, s) from Table 2, in one persistent launch:
+ * every CTA takes matrices from a device work queue (largest first) and runs
+ * steps 1-5 for each.  A[i], C[i], S[i] (host arrays of device pointers) are
+ * row-major n[i] x n[i] FP32 matrices; C[i], S[i] must not overlap any A[j]
+ * or each other.  infos_dev (device array of `count` cs_info) and status_dev
+ * (device array of `count` cs_status: CS_OK, CS_ENONFINITE, CS_ERANGE; the
+ * matrix's C and S are then NaN) may be NULL.  Orders > 256 go through
+ * cossin() one by one.  ws_dev: cossin_batched_workspace_size bytes,
+ * 256-byte aligned, owned by the caller. */
+cs_status cossin_batched_workspace_size(int64_t count, const int64_t* n, size_t* bytes);
+
+/* One-shot: uploads the batch descriptors (synchronises `stream` once) and
+ * launches the persistent kernel with the tile shape the autotuner chose for
+ * this batch signature earlier in the process (or the default). */
+cs_status cossin_batched(int64_t count, const int64_t* n, const float* const* A, float* const* C,
+                         float* const* S, void* ws_dev, size_t ws_bytes, cs_info* infos_dev,
+                         int32_t* status_dev, cossin_stream_t stream);
+
+/* Reusable plan: uploads the descriptors once, optionally autotunes (times
+ * every tile shape / occupancy variant on this batch, keeps the fastest; this
+ * runs the batch several times), and captures the queue reset plus the
+ * persistent launch in a CUDA graph.  Each cossin_batched_plan_launch is one
+ * graph launch on `stream`, recomputing every matrix from its current A.
+ * The pointers and ws_dev must stay valid for the plan's lifetime. */
+typedef struct cossin_batched_plan_st* cossin_batched_plan;
+cs_status cossin_batched_plan_create(int64_t count, const int64_t* n, const float* const* A, float* const* C,
+                                     float* const* S, void* ws_dev, size_t ws_bytes, cs_info* infos_dev,
+                                     int32_t* status_dev, int32_t autotune, cossin_stream_t stream,
+                                     cossin_batched_plan* plan);
+cs_status cossin_batched_plan_launch(cossin_batched_plan plan, cossin_stream_t stream);
+/* The variant the plan runs: CTA tile edge (64 or 128) and CTAs per SM. */
+cs_status cossin_batched_plan_info(cossin_batched_plan plan, int32_t* tile, int32_t* ctas_per_sm);
+cs_status cossin_batched_plan_destroy(cossin_batched_plan plan);
+
 /* Last error message of the calling thread ("" if none). */
 const char* cossin_last_error(void);
 

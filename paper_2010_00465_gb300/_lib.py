@@ -46,6 +46,13 @@ SIGNATURES = {
     "cossin_ex": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp, _sz, _i32, _i32,
                                  ctypes.POINTER(CsInfo), _vp]),
     "cossin_matmul": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
+    "cossin_batched_workspace_size": (ctypes.c_int, [_i64, _vp, ctypes.POINTER(_sz)]),
+    "cossin_batched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp]),
+    "cossin_batched_plan_create": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp, _i32, _vp,
+                                                  ctypes.POINTER(_vp)]),
+    "cossin_batched_plan_launch": (ctypes.c_int, [_vp, _vp]),
+    "cossin_batched_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "cossin_batched_plan_destroy": (ctypes.c_int, [_vp]),
     "cossin_last_error": (ctypes.c_char_p, []),
     "cossin_device_status": (ctypes.c_int, [_vp]),
     "cossin_prof_enable": (None, [_i32]),

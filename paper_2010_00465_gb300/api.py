@@ -116,6 +116,107 @@ def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Te
     return P
 
 
+INFO_DTYPE = None
+
+
+def _info_dtype():
+    import numpy as np
+    return np.dtype([("norm1", "<f8"), ("m", "<i4"), ("s", "<i4"), ("products", "<i4"), ("table", "<i4"),
+                     ("flops", "<f8")])
+
+
+class BatchedPlan:
+    """cos/sin of a list of square FP32 CUDA matrices (orders <= 256), each with
+    its own (2m, s), as one persistent launch replayed from a CUDA graph.
+
+    ``launch()`` recomputes every matrix from the current contents of the
+    inputs; results land in ``self.C`` / ``self.S``; ``infos()`` and
+    ``status()`` read the per-matrix record of the last launch."""
+
+    def __init__(self, mats, autotune: bool = True, stream=None, out=None):
+        import numpy as np
+        self.A = list(mats)
+        for A in self.A:
+            _check_matrix(A, _lib.CS_FP32)
+        count = len(self.A)
+        self.count = count
+        self.n = np.array([A.shape[0] for A in self.A], dtype=np.int64)
+        if out is None:
+            self.C = [torch.empty_like(A) for A in self.A]
+            self.S = [torch.empty_like(A) for A in self.A]
+        else:
+            self.C, self.S = out
+        dev = self.A[0].device if count else torch.device("cuda")
+        self._pa = (ctypes.c_void_p * max(count, 1))(*[A.data_ptr() for A in self.A])
+        self._pc = (ctypes.c_void_p * max(count, 1))(*[C.data_ptr() for C in self.C])
+        self._ps = (ctypes.c_void_p * max(count, 1))(*[S.data_ptr() for S in self.S])
+        size = ctypes.c_size_t()
+        check(lib().cossin_batched_workspace_size(count, self.n.ctypes.data, ctypes.byref(size)))
+        self.ws = torch.empty(max(size.value, 1), dtype=torch.uint8, device=dev)
+        self._infos = torch.zeros(max(count, 1) * 32, dtype=torch.uint8, device=dev)
+        self._status = torch.zeros(max(count, 1), dtype=torch.int32, device=dev)
+        self._plan = ctypes.c_void_p()
+        check(lib().cossin_batched_plan_create(
+            count, self.n.ctypes.data, self._pa, self._pc, self._ps, ctypes.c_void_p(self.ws.data_ptr()),
+            self.ws.numel(), ctypes.c_void_p(self._infos.data_ptr()), ctypes.c_void_p(self._status.data_ptr()),
+            1 if autotune else 0, _stream_ptr(stream), ctypes.byref(self._plan)))
+
+    def launch(self, stream=None):
+        check(lib().cossin_batched_plan_launch(self._plan, _stream_ptr(stream)))
+        return self.C, self.S
+
+    def variant(self):
+        t = ctypes.c_int32()
+        c = ctypes.c_int32()
+        check(lib().cossin_batched_plan_info(self._plan, ctypes.byref(t), ctypes.byref(c)))
+        return {"tile": t.value, "ctas_per_sm": c.value}
+
+    def infos(self):
+        import numpy as np
+        raw = self._infos.cpu().numpy().tobytes()[: 32 * self.count]
+        return np.frombuffer(raw, dtype=_info_dtype())
+
+    def status(self):
+        return self._status[: self.count].cpu().numpy()
+
+    def close(self):
+        if getattr(self, "_plan", None) and self._plan.value:
+            lib().cossin_batched_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cossin_batched(mats, stream=None):
+    """One-shot batched cos/sin (no graph); returns (C list, S list, infos, status)."""
+    import numpy as np
+    mats = list(mats)
+    for A in mats:
+        _check_matrix(A, _lib.CS_FP32)
+    count = len(mats)
+    n = np.array([A.shape[0] for A in mats], dtype=np.int64)
+    C = [torch.empty_like(A) for A in mats]
+    S = [torch.empty_like(A) for A in mats]
+    pa = (ctypes.c_void_p * max(count, 1))(*[A.data_ptr() for A in mats])
+    pc = (ctypes.c_void_p * max(count, 1))(*[X.data_ptr() for X in C])
+    ps = (ctypes.c_void_p * max(count, 1))(*[X.data_ptr() for X in S])
+    size = ctypes.c_size_t()
+    check(lib().cossin_batched_workspace_size(count, n.ctypes.data, ctypes.byref(size)))
+    dev = mats[0].device if count else torch.device("cuda")
+    ws = torch.empty(max(size.value, 1), dtype=torch.uint8, device=dev)
+    infos = torch.zeros(max(count, 1) * 32, dtype=torch.uint8, device=dev)
+    status = torch.zeros(max(count, 1), dtype=torch.int32, device=dev)
+    check(lib().cossin_batched(count, n.ctypes.data, pa, pc, ps, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                               ctypes.c_void_p(infos.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                               _stream_ptr(stream)))
+    inf = np.frombuffer(infos.cpu().numpy().tobytes()[: 32 * count], dtype=_info_dtype())
+    return C, S, inf, status[:count].cpu().numpy()
+
+
 def prof_enable(on: bool = True) -> None:
     lib().cossin_prof_enable(1 if on else 0)
 

@@ -12,6 +12,7 @@
 #include "internal.cuh"
 #include "plan.h"
 #include "tc_gemm.h"
+#include "theta_table.cuh"
 
 namespace cs {
 
@@ -87,21 +88,9 @@ static void prof_drain() {
 }
 
 // -------------------------------------------------------------- selection ---
-// Admissible norms theta_2m of the new Taylor schemes: Table 1 (double,
-// u = 2^-53) and Table 2 (single, u = 2^-24), 2m = 4, 8, 16, 24.  Table 1's
-// k = 7 sine entry reads 1.97, but the printed k = 7 sine coefficients match
-// the series only through A^21; the Sec. 3 error series with them reaches
-// 2^-53 at 1.8555, the value used here.
-static const double kThetaCos[2][4] = {{6.5633e-3, 1.1495e-1, 9.8108e-1, 2.5675},
-                                       {1.8709e-1, 8.5756e-1, 2.9935, 5.5555}};
-static const double kThetaSin[2][4] = {{1.777e-2, 8.0438e-2, 1.1184, 1.8555},
-                                       {3.1386e-1, 7.492e-1, 3.2152, 4.3819}};
-static const int kFamilies[4] = {4, 8, 16, 24};
-static const int kProducts[4] = {3, 4, 6, 7};  // Pi_2m, Tables 1-2
-
 int products_of(int m) {
   for (int f = 0; f < 4; ++f)
-    if (kFamilies[f] == m) return kProducts[f];
+    if (family_order(f) == m) return family_products(f);
   return -1;
 }
 
@@ -109,22 +98,11 @@ cs_status select_ms(double norm1, int table, int* m, int* s) {
   if (table < 0 || table > 1) return fail(CS_EINVAL, "select: table must be 0 (double) or 1 (single)");
   if (!isfinite(norm1)) return fail(CS_ENONFINITE, "select: ||A||_1 is not finite");
   if (norm1 < 0) return fail(CS_EINVAL, "select: negative norm");
-  int best = -1, best_s = 0, best_cost = 1 << 30;
-  for (int f = 0; f < 4; ++f) {
-    const double th = fmin(kThetaCos[table][f], kThetaSin[table][f]);
-    int sf = 0;
-    while (sf <= kMaxS && ldexp(norm1, -sf) > th) ++sf;
-    if (sf > kMaxS) continue;
-    const int cost = kProducts[f] + 2 * sf;
-    if (cost < best_cost || (cost == best_cost && sf < best_s)) {
-      best = f;
-      best_s = sf;
-      best_cost = cost;
-    }
-  }
-  if (best < 0) return fail(CS_ERANGE, "select: ||A||_1 needs more than 64 double-angle steps");
-  *m = kFamilies[best];
-  *s = best_s;
+  int f = 0, sf = 0;
+  if (select_family(norm1, table, &f, &sf) != 0)
+    return fail(CS_ERANGE, "select: ||A||_1 needs more than 64 double-angle steps");
+  *m = family_order(f);
+  *s = sf;
   return CS_OK;
 }
 
