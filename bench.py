@@ -345,7 +345,70 @@ def forms(api, wsp):
                                                 float((Ss - S64).norm() / S64.norm()))
         row["split_speedup_vs_fp64_path"] = row["fp64"]["ms"] / row["split_tf32"]["ms"]
         out["norm%g" % nrm] = row
-    return {"n": N, "family": "normal", "split_tf32": out}
+    return {"n": N, "family": "normal", "split_tf32": out, "batched": batched_form(api)}
+
+
+def batched_form(api, count=20000, reps=5, fp64_sample=240):
+    """The batched workload: 20,000 FP32 matrices, n log-uniform in [8, 256],
+    ||A||_1 log-uniform in [2^-6, 2^6], half symmetric, in one graph-captured
+    persistent launch (autotuned).  Against it: the plain FP64 GPU path, one
+    cossin call per matrix, timed on a random sample and scaled by the
+    sample's share of the batch's algorithmic flops."""
+    import torch
+    import oracle
+    from paper_2010_00465_gb300 import inputs
+    ns, norms, fams = inputs.batch_shapes(count, index=3)
+    host = [inputs.matrix(int(ns[i]), str(fams[i]), float(norms[i]), index=3, sub=i + 1).astype(np.float32)
+            for i in range(count)]
+    dev = [torch.from_numpy(M).cuda() for M in host]
+    plan = api.BatchedPlan(dev, autotune=True)
+    for _ in range(2):
+        plan.launch()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    infos = plan.infos()
+    flops = float(infos["flops"].sum())
+    # accuracy: a few matrices against the oracle (single table, same (m, s))
+    g = inputs.rng(3, 77)
+    errs = []
+    for i in list(np.argsort(-ns)[:2]) + list(g.choice(count, 6, replace=False)):
+        A = host[i].astype(np.float64)
+        Co, So, _ = oracle.cossin(A, "single", m=int(infos[i]["m"]), s=int(infos[i]["s"]))
+        C = plan.C[i].double().cpu().numpy()
+        S = plan.S[i].double().cpu().numpy()
+        errs.append(max(float(np.linalg.norm(C - Co) / np.linalg.norm(Co)),
+                        float(np.linalg.norm(S - So) / max(np.linalg.norm(So), 1e-300))))
+    # plain FP64 GPU path on a sample
+    idx = g.choice(count, fp64_sample, replace=False)
+    d64 = [torch.from_numpy(host[i].astype(np.float64)).cuda() for i in idx]
+    for A in d64[:4]:
+        api.cossin(A, "fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f64_flops = 0.0
+    for A in d64:
+        _, _, inf = api.cossin(A, "fp64", return_info=True)
+        f64_flops += inf["flops"]
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    est64_ms = 1e3 * t64 * (flops / max(f64_flops, 1.0))
+    variant = plan.variant()
+    plan.close()
+    return {"count": count, "ms_per_batch": ms, "matrices_per_s": count / (ms / 1e3),
+            "alg_tflops": flops / (ms / 1e3) / 1e12, "alg_gflop_per_batch": flops / 1e9,
+            "autotuned_variant": variant,
+            "max_rel_err_vs_oracle_sample": max(errs), "sample_size": len(errs),
+            "fp64_plain_path_estimate_ms": est64_ms,
+            "fp64_estimate_method": "%d random matrices through cossin(fp64) one call each, %.2f s, scaled by flops share"
+                                    % (fp64_sample, t64),
+            "speedup_vs_fp64_plain_path": est64_ms / ms}
 
 
 def ncu_case(name):

@@ -135,6 +135,24 @@ cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, voi
 cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec prec, void* P_dev,
                         cossin_stream_t stream);
 
+/* ------------------------------------------------------------ adjoint ---
+ * Reverse mode of the computed approximant (not of the exact functions; the
+ * paper has no adjoint): for each of `count` FP64 n x n matrices (contiguous
+ * [count][n][n] arrays) and cotangents G_C, G_S,
+ *   dA = d/dA ( <G_C, cos_r(A)> + <G_S, sin_r(A)> )
+ * at the (2m, s) the forward pass uses (Table 1, or forced as in cossin_ex,
+ * the same pair for every matrix).  Because the approximant is a polynomial
+ * with real coefficients this equals L_cos(A^T, G_C) + L_sin(A^T, G_S).
+ * The forward pass is recomputed with every product operand kept (the
+ * double-angle levels included); matrices sharing (2m, s) run as one batch.
+ * C, S (nullable) receive cos(A), sin(A) from that forward pass; infos_host
+ * (nullable, host array of `count`) receives each matrix's norm, (2m, s) and
+ * the product count 3 Pi_2m + 6 s of forward plus reverse.  Allocates its
+ * workspace stream-ordered and synchronises `stream` once per (2m, s) group. */
+cs_status cossin_backward(int64_t count, int64_t n, const double* A_dev, const double* G_C_dev,
+                          const double* G_S_dev, double* dA_dev, double* C_dev, double* S_dev,
+                          int32_t force_m, int32_t force_s, cs_info* infos_host, cossin_stream_t stream);
+
 /* ------------------------------------------------------------ batched ---
  * cos and sin of `count` FP32 matrices of orders n[i] <= 256 (host array),
  * each with its own theta, (2m, s) from Table 2, in one persistent launch:

@@ -116,6 +116,75 @@ def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Te
     return P
 
 
+def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m: int | None = None,
+                    s: int | None = None, want_forward: bool = False, stream=None, return_info: bool = False):
+    """Gradient of <G_C, cos(A)> + <G_S, sin(A)> (FP64; A is n x n or a
+    [count, n, n] batch), at the (2m, s) the forward pass uses."""
+    import numpy as np
+    if A.dtype != torch.float64 or G_C.dtype != torch.float64 or G_S.dtype != torch.float64:
+        raise TypeError("the adjoint runs in FP64")
+    batched = A.dim() == 3
+    A3 = A if batched else A.unsqueeze(0)
+    if A3.shape[-1] != A3.shape[-2]:
+        raise ValueError("square matrices expected")
+    A3 = A3.contiguous()
+    GC3 = (G_C if batched else G_C.unsqueeze(0)).contiguous()
+    GS3 = (G_S if batched else G_S.unsqueeze(0)).contiguous()
+    if GC3.shape != A3.shape or GS3.shape != A3.shape:
+        raise ValueError("cotangents must match A")
+    for T in (A3, GC3, GS3):
+        if not T.is_cuda:
+            raise ValueError("CUDA tensors expected")
+    count, n = A3.shape[0], A3.shape[1]
+    dA = torch.empty_like(A3)
+    C = torch.empty_like(A3) if want_forward else None
+    S = torch.empty_like(A3) if want_forward else None
+    infos = (CsInfo * max(count, 1))()
+    fm = -1 if m is None else int(m)
+    fs = -1 if s is None else int(s)
+    check(lib().cossin_backward(count, n, ctypes.c_void_p(A3.data_ptr()), ctypes.c_void_p(GC3.data_ptr()),
+                                ctypes.c_void_p(GS3.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
+                                ctypes.c_void_p(C.data_ptr() if C is not None else 0),
+                                ctypes.c_void_p(S.data_ptr() if S is not None else 0), fm, fs, infos,
+                                _stream_ptr(stream)))
+    if not batched:
+        dA = dA[0]
+        C = C[0] if C is not None else None
+        S = S[0] if S is not None else None
+    out = (dA, C, S) if want_forward else dA
+    if return_info:
+        return out, [infos[i].as_dict() for i in range(count)]
+    return out
+
+
+class CosSin(torch.autograd.Function):
+    """(cos A, sin A) with the library's adjoint as backward (FP64; A is n x n
+    or a [count, n, n] batch).  The backward recomputes the forward pass with
+    its product operands kept, at the same (2m, s)."""
+
+    @staticmethod
+    def forward(ctx, A):
+        if A.dim() == 2:
+            C, S = cossin(A, "fp64")
+        else:
+            outs = [cossin(a, "fp64") for a in A]
+            C = torch.stack([o[0] for o in outs])
+            S = torch.stack([o[1] for o in outs])
+        ctx.save_for_backward(A)
+        return C, S
+
+    @staticmethod
+    def backward(ctx, gC, gS):
+        (A,) = ctx.saved_tensors
+        gC = torch.zeros_like(A) if gC is None else gC.contiguous()
+        gS = torch.zeros_like(A) if gS is None else gS.contiguous()
+        return cossin_backward(A, gC, gS)
+
+
+def cossin_autograd(A: torch.Tensor):
+    return CosSin.apply(A)
+
+
 INFO_DTYPE = None
 
 

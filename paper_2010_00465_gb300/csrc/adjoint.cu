@@ -1,0 +1,349 @@
+// adjoint.cu -- reverse mode of the approximant at fixed (2m, s), FP64.
+//
+// The computed cos and sin are polynomials r_c(A), r_s(A) evaluated by the
+// product plans of the factorised schemes (Sec. 2.1) and the double-angle
+// steps (Sec. 1).  For a loss <G_C, r_c(A)> + <G_S, r_s(A)> the gradient is
+// obtained by running the plans backwards:
+//   * the forward pass is re-run in write-once form, keeping every operand of
+//     every product (the tape; the s double-angle levels C_j, S_j included);
+//   * each step's epilogue is linear, so its adjoint needs only the
+//     coefficients: an elementwise kernel turns the adjoints of the step's
+//     outputs into P^ (adjoint of the product) and adds into the adjoints of
+//     the step's inputs;
+//   * each product P = X Y adds P^ Y^T into X^ and X^T P^ into Y^
+//     (FP64 products with transposed operands and accumulating epilogues);
+//   * a double-angle step C' = 2 C C - I, S' = 2 S C adds
+//     2 (C'^ C^T + C^T C'^) + 2 S^T S'^ into C^ and 2 S'^ C^T into S^.
+// Matrices that share (2m, s) are gathered and processed as one batch.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "internal.cuh"
+#include "plan.h"
+#include "theta_table.cuh"
+
+namespace cs {
+namespace {
+
+struct AdjStep {
+  int32_t nout = 0, nin = 0;
+  const double* adj_out[EPI_MAX_OUT] = {};  // null: that output's adjoint is zero
+  double* adj_in[EPI_MAX_IN] = {};
+  double* phat = nullptr;
+  double alpha[EPI_MAX_OUT] = {};
+  double beta[EPI_MAX_OUT][EPI_MAX_IN] = {};
+  double delta[EPI_MAX_OUT][EPI_MAX_OUT] = {};
+};
+
+// Elementwise adjoint of one epilogue over `total` elements (all arrays share
+// one layout).  Outputs are visited last to first so that adjoints reaching an
+// output through a later output's delta term are complete when it is used.
+__global__ void __launch_bounds__(256) epilogue_adjoint(const AdjStep a, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double tot[EPI_MAX_OUT];
+    double ph = 0.0;
+#pragma unroll
+    for (int t = EPI_MAX_OUT - 1; t >= 0; --t) {
+      if (t >= a.nout) continue;
+      double v = a.adj_out[t] ? a.adj_out[t][i] : 0.0;
+#pragma unroll
+      for (int u = EPI_MAX_OUT - 1; u > 0; --u)
+        if (u > t && u < a.nout) v += a.delta[u][t] * tot[u];
+      tot[t] = v;
+      ph += a.alpha[t] * v;
+    }
+    a.phat[i] = ph;
+#pragma unroll
+    for (int q = 0; q < EPI_MAX_IN; ++q) {
+      if (q >= a.nin) break;
+      double g = 0.0;
+#pragma unroll
+      for (int t = 0; t < EPI_MAX_OUT; ++t)
+        if (t < a.nout) g += a.beta[t][q] * tot[t];
+      a.adj_in[q][i] += g;
+    }
+  }
+}
+
+__global__ void gather_kernel(const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ idx,
+                              int64_t n2, int64_t count) {
+  const int64_t total = n2 * count;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / n2, r = e - b * n2;
+    dst[e] = src[(int64_t)idx[b] * n2 + r];
+  }
+}
+
+__global__ void scatter_kernel(const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ idx,
+                               int64_t n2, int64_t count) {
+  const int64_t total = n2 * count;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / n2, r = e - b * n2;
+    dst[(int64_t)idx[b] * n2 + r] = src[e];
+  }
+}
+
+int blocks_for(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256, 152 * 8); }
+
+// Write-once form of a plan: value ids for every step output.
+struct SsaStep {
+  int X, Y;                 // value ids of the operands
+  std::vector<int> out;     // value id per output
+  std::vector<int> in;      // value ids of the distinct epilogue inputs
+  Epilogue<double> coef;    // alpha, gamma, beta (indexed by `in`), delta
+};
+
+struct Ssa {
+  int nvalues = 0;
+  int A = 0, C = -1, S = -1;
+  std::vector<SsaStep> steps;
+};
+
+Ssa make_ssa(int m, int s) {
+  Ssa g;
+  int cur[SL_COUNT];
+  for (int k = 0; k < SL_COUNT; ++k) cur[k] = -1;
+  g.A = g.nvalues++;
+  cur[SL_A] = g.A;
+  for (const Step& st : chain_plan(m, s)) {
+    SsaStep q;
+    q.X = cur[st.X];
+    q.Y = cur[st.Y];
+    for (size_t t = 0; t < st.outs.size(); ++t) {
+      const OutSpec& o = st.outs[t];
+      q.coef.alpha[t] = o.alpha;
+      q.coef.gamma[t] = o.gamma;
+      for (auto& b : o.beta) {
+        const int v = cur[b.first];
+        int qi = -1;
+        for (size_t k = 0; k < q.in.size(); ++k)
+          if (q.in[k] == v) qi = (int)k;
+        if (qi < 0) {
+          qi = (int)q.in.size();
+          q.in.push_back(v);
+        }
+        q.coef.beta[t][qi] = b.second;
+      }
+      for (auto& d : o.delta) q.coef.delta[t][d.first] = d.second;
+    }
+    for (size_t t = 0; t < st.outs.size(); ++t) q.out.push_back(g.nvalues++);
+    for (size_t t = 0; t < st.outs.size(); ++t) cur[st.outs[t].slot] = q.out[t];
+    q.coef.n_out = (int)st.outs.size();
+    q.coef.n_in = (int)q.in.size();
+    g.steps.push_back(q);
+  }
+  g.C = cur[SL_C];
+  g.S = cur[SL_S];
+  return g;
+}
+
+// Accumulating product: Acc += op(X) op(Y), batched with stride n^2.
+cs_status gemm_acc(const double* X, bool tX, const double* Y, bool tY, double* Acc, double scale, int64_t n,
+                   int64_t batch, cudaStream_t stream) {
+  Epilogue<double> e;
+  e.n_in = 1;
+  e.in[0] = Acc;
+  e.n_out = 1;
+  e.out[0] = Acc;
+  e.alpha[0] = scale;
+  e.beta[0][0] = 1.0;
+  const int64_t n2 = n * n;
+  return gemm_f64(X, Y, n, n, n, n, n, tX, tY, e, n, batch, n2, n2, n2, stream);
+}
+
+cs_status run_group(const double* A, const double* GC, const double* GS, double* dA, double* C_out, double* S_out,
+                    int64_t n, int m, int s, int64_t g, cudaStream_t stream) {
+  const Ssa ssa = make_ssa(m, s);
+  const int64_t n2 = n * n;
+  const int nlev = s + 1;
+  // values: chain values, then the double-angle levels C_1..C_s, S_1..S_s
+  const int nval = ssa.nvalues + 2 * s;
+  auto levC = [&](int j) { return j == 0 ? ssa.C : ssa.nvalues + (j - 1); };
+  auto levS = [&](int j) { return j == 0 ? ssa.S : ssa.nvalues + s + (j - 1); };
+  (void)nlev;
+  const size_t per = sizeof(double) * (size_t)n2 * (size_t)g;
+  const size_t total = per * (size_t)(2 * nval + 1);
+  char* buf = nullptr;
+  CS_CUDA_CHECK(cudaMallocAsync((void**)&buf, total, stream));
+  auto val = [&](int v) { return (double*)(buf + per * (size_t)v); };
+  auto adj = [&](int v) { return (double*)(buf + per * (size_t)(nval + v)); };
+  double* phat = (double*)(buf + per * (size_t)(2 * nval));
+  cs_status rc = CS_OK;
+  cudaError_t ce = cudaMemsetAsync(buf + per * (size_t)nval, 0, per * (size_t)nval, stream);
+  if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemsetAsync");
+  if (rc == CS_OK) ce = cudaMemcpyAsync(val(ssa.A), A, per, cudaMemcpyDeviceToDevice, stream);
+  if (rc == CS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
+  // ---- forward, write-once
+  for (size_t i = 0; rc == CS_OK && i < ssa.steps.size(); ++i) {
+    const SsaStep& q = ssa.steps[i];
+    Epilogue<double> e = q.coef;
+    for (int k = 0; k < e.n_in; ++k) e.in[k] = val(q.in[k]);
+    for (int t = 0; t < e.n_out; ++t) e.out[t] = val(q.out[t]);
+    rc = gemm_f64(val(q.X), val(q.Y), n, n, n, n, n, false, false, e, n, g, n2, n2, n2, stream);
+  }
+  for (int j = 0; rc == CS_OK && j < s; ++j) {
+    Epilogue<double> ec;
+    ec.n_out = 1;
+    ec.out[0] = val(levC(j + 1));
+    ec.alpha[0] = 2.0;
+    ec.gamma[0] = -1.0;
+    rc = gemm_f64(val(levC(j)), val(levC(j)), n, n, n, n, n, false, false, ec, n, g, n2, n2, n2, stream);
+    if (rc != CS_OK) break;
+    Epilogue<double> es;
+    es.n_out = 1;
+    es.out[0] = val(levS(j + 1));
+    es.alpha[0] = 2.0;
+    rc = gemm_f64(val(levS(j)), val(levC(j)), n, n, n, n, n, false, false, es, n, g, n2, n2, n2, stream);
+  }
+  if (rc == CS_OK && C_out) ce = cudaMemcpyAsync(C_out, val(levC(s)), per, cudaMemcpyDeviceToDevice, stream);
+  if (rc == CS_OK && S_out && ce == cudaSuccess) ce = cudaMemcpyAsync(S_out, val(levS(s)), per, cudaMemcpyDeviceToDevice, stream);
+  if (rc == CS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
+  // ---- reverse
+  if (rc == CS_OK) ce = cudaMemcpyAsync(adj(levC(s)), GC, per, cudaMemcpyDeviceToDevice, stream);
+  if (rc == CS_OK && ce == cudaSuccess) ce = cudaMemcpyAsync(adj(levS(s)), GS, per, cudaMemcpyDeviceToDevice, stream);
+  if (rc == CS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
+  for (int j = s - 1; rc == CS_OK && j >= 0; --j) {
+    const double* C = val(levC(j));
+    const double* S = val(levS(j));
+    const double* Ch = adj(levC(j + 1));
+    const double* Sh = adj(levS(j + 1));
+    double* Cj = adj(levC(j));
+    double* Sj = adj(levS(j));
+    rc = gemm_acc(Ch, false, C, true, Cj, 2.0, n, g, stream);                  // 2 C'^ C^T
+    if (rc == CS_OK) rc = gemm_acc(C, true, Ch, false, Cj, 2.0, n, g, stream);  // 2 C^T C'^
+    if (rc == CS_OK) rc = gemm_acc(S, true, Sh, false, Cj, 2.0, n, g, stream);  // 2 S^T S'^
+    if (rc == CS_OK) rc = gemm_acc(Sh, false, C, true, Sj, 2.0, n, g, stream);  // 2 S'^ C^T
+  }
+  for (int i = (int)ssa.steps.size() - 1; rc == CS_OK && i >= 0; --i) {
+    const SsaStep& q = ssa.steps[i];
+    AdjStep a;
+    a.nout = q.coef.n_out;
+    a.nin = q.coef.n_in;
+    for (int t = 0; t < a.nout; ++t) {
+      a.adj_out[t] = adj(q.out[t]);
+      a.alpha[t] = q.coef.alpha[t];
+      for (int k = 0; k < a.nin; ++k) a.beta[t][k] = q.coef.beta[t][k];
+      for (int u = 0; u < a.nout; ++u) a.delta[t][u] = q.coef.delta[t][u];
+    }
+    for (int k = 0; k < a.nin; ++k) a.adj_in[k] = adj(q.in[k]);
+    a.phat = phat;
+    const int64_t tot = n2 * g;
+    epilogue_adjoint<<<blocks_for(tot), 256, 0, stream>>>(a, tot);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(ce, "epilogue_adjoint");
+      break;
+    }
+    rc = gemm_acc(phat, false, val(q.Y), true, adj(q.X), 1.0, n, g, stream);            // X^ += P^ Y^T
+    if (rc == CS_OK) rc = gemm_acc(val(q.X), true, phat, false, adj(q.Y), 1.0, n, g, stream);  // Y^ += X^T P^
+  }
+  if (rc == CS_OK) ce = cudaMemcpyAsync(dA, adj(ssa.A), per, cudaMemcpyDeviceToDevice, stream);
+  if (rc == CS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
+  cudaFreeAsync(buf, stream);
+  return rc;
+}
+
+}  // namespace
+
+int64_t adjoint_products(int m, int s) { return 3 * products_of(m) + 6 * s; }
+
+}  // namespace cs
+
+extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, const double* G_C,
+                                     const double* G_S, double* dA, double* C, double* S, int32_t force_m,
+                                     int32_t force_s, cs_info* infos_host, cossin_stream_t stream) {
+  using namespace cs;
+  if (count < 0 || n < 0 || n > kMaxN) return fail(CS_EINVAL, "count or n out of range");
+  if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");
+  if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 16 or 24");
+  if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_s must be in [0, 64]");
+  if (count == 0 || n == 0) return CS_OK;
+  if (!A || !G_C || !G_S || !dA) return fail(CS_EINVAL, "null matrix pointer");
+  const int64_t n2 = n * n;
+  const size_t bytes = sizeof(double) * (size_t)n2 * (size_t)count;
+  auto ov = [&](const void* a, const void* b) {
+    return a && b && (const char*)a < (const char*)b + bytes && (const char*)b < (const char*)a + bytes;
+  };
+  if (ov(dA, A) || ov(dA, G_C) || ov(dA, G_S) || ov(C, A) || ov(S, A) || ov(C, S) || ov(C, dA) || ov(S, dA))
+    return fail(CS_EINVAL, "outputs must not overlap inputs or each other");
+  cudaStream_t st = (cudaStream_t)stream;
+  // norms of every matrix, one synchronisation
+  std::vector<double> norms((size_t)count);
+  {
+    const size_t part = sizeof(double) * ((size_t)norm1_scratch_elems(n) + (size_t)count);
+    char* nb = nullptr;
+    CS_CUDA_CHECK(cudaMallocAsync((void**)&nb, part, st));
+    double* outs = (double*)nb;
+    double* partial = outs + count;
+    cs_status rc = CS_OK;
+    for (int64_t b = 0; rc == CS_OK && b < count; ++b) rc = norm1_f64(A + b * n2, n, partial, outs + b, st);
+    cudaError_t ce = rc == CS_OK ? cudaMemcpyAsync(norms.data(), outs, sizeof(double) * count, cudaMemcpyDeviceToHost, st)
+                                 : cudaSuccess;
+    cudaError_t ce2 = cudaStreamSynchronize(st);
+    cudaFreeAsync(nb, st);
+    if (rc != CS_OK) return rc;
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpyAsync");
+    if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");
+  }
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int64_t b = 0; b < count; ++b) {
+    int m, s;
+    if (force_m == -1) {
+      CS_CHECK(select_ms(norms[b], 0, &m, &s));
+    } else {
+      if (!isfinite(norms[b])) return fail(CS_ENONFINITE, "||A||_1 is not finite");
+      m = force_m;
+      s = force_s;
+    }
+    groups[{m, s}].push_back((int)b);
+    if (infos_host) {
+      const int prods = (int)adjoint_products(m, s);
+      infos_host[b] = cs_info{norms[b], m, s, prods, 0, 2.0 * (double)n * n * n * prods};
+    }
+  }
+  for (auto& kv : groups) {
+    const int m = kv.first.first, s = kv.first.second;
+    const std::vector<int>& idx = kv.second;
+    const int64_t g = (int64_t)idx.size();
+    const size_t per = sizeof(double) * (size_t)n2 * (size_t)g;
+    const bool need_c = C != nullptr, need_s = S != nullptr;
+    char* gb = nullptr;
+    CS_CUDA_CHECK(cudaMallocAsync((void**)&gb, 6 * per + sizeof(int) * g, st));
+    double* gA = (double*)gb;
+    double* gGC = (double*)(gb + per);
+    double* gGS = (double*)(gb + 2 * per);
+    double* gdA = (double*)(gb + 3 * per);
+    double* gC = (double*)(gb + 4 * per);
+    double* gS = (double*)(gb + 5 * per);
+    int* didx = (int*)(gb + 6 * per);
+    cs_status rc = CS_OK;
+    cudaError_t ce = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * g, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
+    const int nb = blocks_for(n2 * g);
+    if (rc == CS_OK) {
+      gather_kernel<<<nb, 256, 0, st>>>(A, gA, didx, n2, g);
+      gather_kernel<<<nb, 256, 0, st>>>(G_C, gGC, didx, n2, g);
+      gather_kernel<<<nb, 256, 0, st>>>(G_S, gGS, didx, n2, g);
+      ce = cudaGetLastError();
+      if (ce != cudaSuccess) rc = cuda_fail(ce, "gather");
+    }
+    if (rc == CS_OK) rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, st);
+    if (rc == CS_OK) {
+      scatter_kernel<<<nb, 256, 0, st>>>(gdA, dA, didx, n2, g);
+      if (need_c) scatter_kernel<<<nb, 256, 0, st>>>(gC, C, didx, n2, g);
+      if (need_s) scatter_kernel<<<nb, 256, 0, st>>>(gS, S, didx, n2, g);
+      ce = cudaGetLastError();
+      if (ce != cudaSuccess) rc = cuda_fail(ce, "scatter");
+    }
+    // the host index vector must outlive its copy
+    cudaError_t ce2 = cudaStreamSynchronize(st);
+    cudaFreeAsync(gb, st);
+    if (rc != CS_OK) return rc;
+    if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");
+  }
+  return CS_OK;
+}
