@@ -183,7 +183,7 @@ def main():
     ap.add_argument("--precisions", default=None, help="comma list: fp64,fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the split-precision comparison")
-    ap.add_argument("--ncu-case", default=None, choices=["gemm_tf32", "gemm_f64", "norm1"],
+    ap.add_argument("--ncu-case", default=None, choices=["gemm_tf32", "gemm_f64", "norm1", "batched", "batched256"],
                     help="run one small launch set for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -446,6 +446,23 @@ def ncu_case(name):
     if name == "gemm_tf32":
         A = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).float().cuda()
         api.cossin(A, "fp32")
+    elif name == "batched":
+        # 2,000 matrices of the batched workload's distribution, one launch
+        ns, norms, fams = inputs.batch_shapes(2000, index=3)
+        dev = [torch.from_numpy(inputs.matrix(int(ns[i]), str(fams[i]), float(norms[i]), index=3,
+                                              sub=i + 1).astype(np.float32)).cuda() for i in range(2000)]
+        plan = api.BatchedPlan(dev, autotune=False)
+        plan.launch()
+        torch.cuda.synchronize()
+        plan.close()
+    elif name == "batched256":
+        # 304 matrices of order 256 (the largest of the batched workload), one launch
+        dev = [torch.from_numpy(inputs.matrix(256, "normal", 8.0, index=3, sub=i + 1).astype(np.float32)).cuda()
+               for i in range(304)]
+        plan = api.BatchedPlan(dev, autotune=False)
+        plan.launch()
+        torch.cuda.synchronize()
+        plan.close()
     elif name == "gemm_f64":
         X = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
         api.matmul(X, X, "fp64")

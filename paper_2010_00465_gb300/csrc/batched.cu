@@ -8,8 +8,8 @@
 // fused into each product's epilogue, then s double-angle products
 // [C; S] C.  Orders are at most kMaxOrder = 256, so the products are CTA-level
 // FP32 FMA tiles (IEEE accumulation; intermediates stay in the CTA's own
-// workspace slice, hot in L2).  Two tile shapes (64 and 128 rows/columns per
-// CTA tile) and two occupancies are timed by the plan's autotuner.
+// workspace slice, hot in L2).  Tile shapes (64 or 128 rows/columns per CTA
+// tile for orders above 64) and occupancies are timed by the plan's autotuner.
 //
 // Graph capture: the plan records the queue reset and the persistent launch
 // in a CUDA graph once; each replay is one graph launch.
@@ -35,21 +35,19 @@ constexpr int kMaxOrder = 256;
 constexpr int kBK = 16;
 constexpr int kSlots = 8 + 4;  // W0..W7 and two stacked [C; S] buffers (2 each)
 
-struct DOut {
-  int slot;
-  int scale;  // 0: none, 1: x 4^-s (first product), 2: x 2^-s (sine product)
-  float alpha;
-  float gamma;
-  int nb;
-  int bslot[EPI_MAX_IN];
-  float bcoef[EPI_MAX_IN];
-  int nd;
-  int dout[EPI_MAX_OUT];
-  float dcoef[EPI_MAX_OUT];
-};
+// One product of a plan in dense form: distinct input slots in[], and for
+// every output t: out_t = alpha_t P + gamma_t I + sum_q beta[t][q] in_q
+// + sum_{u<t} delta[t][u] out_u; scale[t] multiplies alpha_t by 4^-s (1) or
+// 2^-s (2).
 struct DStep {
-  int X, Y, nout;
-  DOut out[EPI_MAX_OUT];
+  int X, Y, nout, nin;
+  int out[EPI_MAX_OUT];
+  int in[EPI_MAX_IN];
+  int scale[EPI_MAX_OUT];
+  float alpha[EPI_MAX_OUT];
+  float gamma[EPI_MAX_OUT];
+  float beta[EPI_MAX_OUT][EPI_MAX_IN];
+  float delta[EPI_MAX_OUT][EPI_MAX_OUT];
 };
 struct DPlan {
   int nsteps;
@@ -97,12 +95,38 @@ __device__ double block_norm1(const float* __restrict__ A, int n, double* red) {
 // matrix) in tiles of T x T; the epilogue is either a plan step (st != null)
 // or the stacked double-angle form (rows < split to outC as 2X - I, the rest
 // to outS as 2X).
+//
+// 256 threads as 16 x 16; thread (ty, tx) owns rows {ty*H + i, T/2 + ty*H + i}
+// and columns {tx*H + j, T/2 + tx*H + j}, H = T/32, so that its operands are
+// read from shared memory as float4 without bank conflicts.  The k-panels
+// (kBK deep) are double-buffered: the next panel is fetched from global
+// memory into registers while the current one is multiplied.
 template <int T>
 __device__ void cta_product(const float* __restrict__ X, const float* __restrict__ Y, int M, int N, int K, int ld,
                             const DStep* st, const Slots& sl, float a2, float as, int split, float* outC,
-                            float* outS, float (*Xs)[T + 4], float (*Ys)[T + 4]) {
-  constexpr int R = T / 16;  // micro-tile R x R per thread (16 x 16 threads)
+                            float* outS, float* smem) {
+  constexpr int H = T / 32;      // half micro-tile edge: 4 (T = 128) or 2 (T = 64)
+  constexpr int R = 2 * H;       // micro-tile edge
+  constexpr int LD = T + 4;      // shared-memory row pitch (floats)
+  constexpr int PER = (T * kBK) / kThreads;  // panel elements per thread per operand
+  float (*Xs)[kBK][LD] = reinterpret_cast<float (*)[kBK][LD]>(smem);           // [2][kBK][LD]
+  float (*Ys)[kBK][LD] = reinterpret_cast<float (*)[kBK][LD]>(smem + 2 * kBK * LD);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float* inp[EPI_MAX_IN];
+  float* outp[EPI_MAX_OUT];
+  float alph[EPI_MAX_OUT];
+  int nin = 0, nout = 0;
+  if (st) {
+    nin = st->nin;
+    nout = st->nout;
+#pragma unroll
+    for (int q = 0; q < EPI_MAX_IN; ++q) inp[q] = q < nin ? sl.p[st->in[q]] : nullptr;
+#pragma unroll
+    for (int t = 0; t < EPI_MAX_OUT; ++t) {
+      outp[t] = t < nout ? sl.p[st->out[t]] : nullptr;
+      alph[t] = st->scale[t] == 1 ? st->alpha[t] * a2 : st->scale[t] == 2 ? st->alpha[t] * as : st->alpha[t];
+    }
+  }
   for (int m0 = 0; m0 < M; m0 += T) {
     for (int n0 = 0; n0 < N; n0 += T) {
       float acc[R][R];
@@ -110,40 +134,70 @@ __device__ void cta_product(const float* __restrict__ X, const float* __restrict
       for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[i][j] = 0.f;
+      float xr[PER], yr[PER];
+#define CS_BT_FETCH(k0_)                                                     \
+  _Pragma("unroll") for (int t = 0; t < PER; ++t) {                          \
+    const int e = tid + t * kThreads;                                        \
+    const int mm = e / kBK, kk = e % kBK;                                    \
+    const int gm = m0 + mm, gk = (k0_) + kk;                                 \
+    xr[t] = (gm < M && gk < K) ? X[(int64_t)gm * ld + gk] : 0.f;             \
+    const int kk2 = e / T, nn = e % T;                                       \
+    const int gk2 = (k0_) + kk2, gn = n0 + nn;                               \
+    yr[t] = (gk2 < K && gn < N) ? Y[(int64_t)gk2 * ld + gn] : 0.f;           \
+  }
+#define CS_BT_STASH(buf_)                                                    \
+  _Pragma("unroll") for (int t = 0; t < PER; ++t) {                          \
+    const int e = tid + t * kThreads;                                        \
+    Xs[(buf_)][e % kBK][e / kBK] = xr[t];                                    \
+    Ys[(buf_)][e / T][e % T] = yr[t];                                        \
+  }
+      CS_BT_FETCH(0)
+      CS_BT_STASH(0)
+      __syncthreads();
+      int buf = 0;
       for (int k0 = 0; k0 < K; k0 += kBK) {
-#pragma unroll
-        for (int t = 0; t < (T * kBK) / kThreads; ++t) {
-          const int e = tid + t * kThreads;
-          const int mm = e / kBK, kk = e % kBK;
-          const int gm = m0 + mm, gk = k0 + kk;
-          Xs[kk][mm] = (gm < M && gk < K) ? X[(int64_t)gm * ld + gk] : 0.f;
-          const int kk2 = e / T, nn = e % T;
-          const int gk2 = k0 + kk2, gn = n0 + nn;
-          Ys[kk2][nn] = (gk2 < K && gn < N) ? Y[(int64_t)gk2 * ld + gn] : 0.f;
+        const bool more = k0 + kBK < K;
+        if (more) {
+          CS_BT_FETCH(k0 + kBK)
         }
-        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
           float a[R], b[R];
 #pragma unroll
-          for (int i = 0; i < R; ++i) {
-            a[i] = Xs[kk][ty * R + i];
-            b[i] = Ys[kk][tx * R + i];
+          for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int q = 0; q < H; q += 4 > H ? H : 4) {
+              if (H >= 4) {
+                const float4 va = *reinterpret_cast<const float4*>(&Xs[buf][kk][h * (T / 2) + ty * H + q]);
+                const float4 vb = *reinterpret_cast<const float4*>(&Ys[buf][kk][h * (T / 2) + tx * H + q]);
+                a[h * H + q] = va.x; a[h * H + q + 1] = va.y; a[h * H + q + 2] = va.z; a[h * H + q + 3] = va.w;
+                b[h * H + q] = vb.x; b[h * H + q + 1] = vb.y; b[h * H + q + 2] = vb.z; b[h * H + q + 3] = vb.w;
+              } else {
+                const float2 va = *reinterpret_cast<const float2*>(&Xs[buf][kk][h * (T / 2) + ty * H]);
+                const float2 vb = *reinterpret_cast<const float2*>(&Ys[buf][kk][h * (T / 2) + tx * H]);
+                a[h * H] = va.x; a[h * H + 1] = va.y;
+                b[h * H] = vb.x; b[h * H + 1] = vb.y;
+              }
+            }
           }
 #pragma unroll
           for (int i = 0; i < R; ++i)
 #pragma unroll
             for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        __syncthreads();
+        if (more) {
+          CS_BT_STASH(buf ^ 1)
+          __syncthreads();
+          buf ^= 1;
+        }
       }
-#pragma unroll
+#pragma unroll 1
       for (int i = 0; i < R; ++i) {
-        const int r = m0 + ty * R + i;
+        const int r = m0 + (i < H ? ty * H + i : T / 2 + ty * H + (i - H));
         if (r >= M) continue;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int c = n0 + tx * R + j;
+          const int c = n0 + (j < H ? tx * H + j : T / 2 + tx * H + (j - H));
           if (c >= N) continue;
           const float p = acc[i][j];
           if (!st) {
@@ -152,35 +206,38 @@ __device__ void cta_product(const float* __restrict__ X, const float* __restrict
             continue;
           }
           const int64_t idx = (int64_t)r * ld + c;
-          float o[EPI_MAX_OUT];
+          float in[EPI_MAX_IN], o[EPI_MAX_OUT];
+#pragma unroll
+          for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < nin ? inp[q][idx] : 0.f;
 #pragma unroll
           for (int t = 0; t < EPI_MAX_OUT; ++t) {
-            if (t >= st->nout) break;
-            const DOut& d = st->out[t];
-            const float alpha = d.scale == 1 ? d.alpha * a2 : d.scale == 2 ? d.alpha * as : d.alpha;
-            float v = alpha * p + (r == c ? d.gamma : 0.f);
-            for (int q = 0; q < d.nb; ++q) v = fmaf(d.bcoef[q], sl.p[d.bslot[q]][idx], v);
-            for (int u = 0; u < d.nd; ++u) v = fmaf(d.dcoef[u], o[d.dout[u]], v);
+            if (t >= nout) break;
+            float v = alph[t] * p + (r == c ? st->gamma[t] : 0.f);
+#pragma unroll
+            for (int q = 0; q < EPI_MAX_IN; ++q)
+              if (q < nin) v = fmaf(st->beta[t][q], in[q], v);
+#pragma unroll
+            for (int u = 0; u < t; ++u) v = fmaf(st->delta[t][u], o[u], v);
             o[t] = v;
           }
 #pragma unroll
-          for (int t = 0; t < EPI_MAX_OUT; ++t) {
-            if (t >= st->nout) break;
-            sl.p[st->out[t].slot][idx] = o[t];
-          }
+          for (int t = 0; t < EPI_MAX_OUT; ++t)
+            if (t < nout) outp[t][idx] = o[t];
         }
       }
+      __syncthreads();  // the next tile overwrites both panel buffers
     }
   }
-  __syncthreads();
+#undef CS_BT_FETCH
+#undef CS_BT_STASH
 }
 
+// T is the tile edge for orders above 64; orders <= 64 always use 64-wide tiles.
 template <int T>
-__global__ void __launch_bounds__(kThreads) batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order,
+__global__ void __launch_bounds__(kThreads, T == 128 ? 1 : 2) batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order,
                                                            int count, int* queue, float* ws_all, int64_t ws_per_cta,
                                                            cs_info* infos, int32_t* status) {
-  __shared__ float Xs[kBK][T + 4];
-  __shared__ float Ys[kBK][T + 4];
+  __shared__ __align__(16) float panels[4 * kBK * (T + 4)];
   __shared__ double red[kThreads / 32];
   __shared__ int item;
   float* ws = ws_all + (int64_t)blockIdx.x * ws_per_cta;
@@ -232,14 +289,21 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const Desc* __restric
     const DPlan& P = c_plans[f];
     for (int k = 0; k < P.nsteps; ++k) {
       const DStep* st = &P.step[k];
-      cta_product<T>(sl.p[st->X], sl.p[st->Y], n, n, n, n, st, sl, a2, as, 0, nullptr, nullptr, Xs, Ys);
+      if (T == 128 && n > 64)
+        cta_product<128>(sl.p[st->X], sl.p[st->Y], n, n, n, n, st, sl, a2, as, 0, nullptr, nullptr, panels);
+      else
+        cta_product<64>(sl.p[st->X], sl.p[st->Y], n, n, n, n, st, sl, a2, as, 0, nullptr, nullptr, panels);
     }
     for (int q = 0; q < s; ++q) {
       float* cur = (q & 1) ? ping1 : ping0;
       float* nxt = (q & 1) ? ping0 : ping1;
       const bool last = q == s - 1;
-      cta_product<T>(cur, cur, 2 * n, n, n, n, nullptr, sl, 0.f, 0.f, n, last ? d.C : nxt, last ? d.S : nxt + n2,
-                     Xs, Ys);
+      if (T == 128 && n > 64)
+        cta_product<128>(cur, cur, 2 * n, n, n, n, nullptr, sl, 0.f, 0.f, n, last ? d.C : nxt,
+                         last ? d.S : nxt + n2, panels);
+      else
+        cta_product<64>(cur, cur, 2 * n, n, n, n, nullptr, sl, 0.f, 0.f, n, last ? d.C : nxt,
+                        last ? d.S : nxt + n2, panels);
     }
   }
 }
@@ -249,7 +313,7 @@ struct Variant {
   int tile;
   int ctas_per_sm;
 };
-const Variant kVariants[] = {{128, 1}, {128, 2}, {64, 2}, {64, 4}};
+const Variant kVariants[] = {{128, 1}, {64, 2}, {64, 1}};
 
 std::mutex g_mu;
 bool g_plans_uploaded[64] = {};
@@ -269,26 +333,27 @@ cs_status upload_plans() {
     P.nsteps = (int)steps.size();
     for (size_t k = 0; k < steps.size(); ++k) {
       DStep& D = P.step[k];
+      D = DStep{};
       D.X = steps[k].X;
       D.Y = steps[k].Y;
       D.nout = (int)steps[k].outs.size();
       for (int t = 0; t < D.nout; ++t) {
         const OutSpec& o = steps[k].outs[t];
-        DOut& q = D.out[t];
-        q.slot = o.slot;
-        q.alpha = (float)o.alpha;
-        q.gamma = (float)o.gamma;
-        q.scale = (k == 0) ? 1 : (o.slot == SL_S ? 2 : 0);
-        q.nb = (int)o.beta.size();
-        for (int b = 0; b < q.nb; ++b) {
-          q.bslot[b] = o.beta[b].first;
-          q.bcoef[b] = (float)o.beta[b].second;
+        D.out[t] = o.slot;
+        D.alpha[t] = (float)o.alpha;
+        D.gamma[t] = (float)o.gamma;
+        D.scale[t] = (k == 0) ? 1 : (o.slot == SL_S ? 2 : 0);
+        for (auto& b : o.beta) {
+          int q = -1;
+          for (int z = 0; z < D.nin; ++z)
+            if (D.in[z] == b.first) q = z;
+          if (q < 0) {
+            q = D.nin++;
+            D.in[q] = b.first;
+          }
+          D.beta[t][q] = (float)b.second;
         }
-        q.nd = (int)o.delta.size();
-        for (int u = 0; u < q.nd; ++u) {
-          q.dout[u] = o.delta[u].first;
-          q.dcoef[u] = (float)o.delta[u].second;
-        }
+        for (auto& d : o.delta) D.delta[t][d.first] = (float)d.second;
       }
     }
   }
