@@ -274,17 +274,13 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
   // norms of every matrix, one synchronisation
   std::vector<double> norms((size_t)count);
   {
-    const size_t part = sizeof(double) * ((size_t)norm1_scratch_elems(n) + (size_t)count);
-    char* nb = nullptr;
-    CS_CUDA_CHECK(cudaMallocAsync((void**)&nb, part, st));
-    double* outs = (double*)nb;
-    double* partial = outs + count;
-    cs_status rc = CS_OK;
-    for (int64_t b = 0; rc == CS_OK && b < count; ++b) rc = norm1_f64(A + b * n2, n, partial, outs + b, st);
+    double* outs = nullptr;
+    CS_CUDA_CHECK(cudaMallocAsync((void**)&outs, sizeof(double) * count, st));
+    cs_status rc = norm1_batched_f64(A, n, count, outs, st);
     cudaError_t ce = rc == CS_OK ? cudaMemcpyAsync(norms.data(), outs, sizeof(double) * count, cudaMemcpyDeviceToHost, st)
                                  : cudaSuccess;
     cudaError_t ce2 = cudaStreamSynchronize(st);
-    cudaFreeAsync(nb, st);
+    cudaFreeAsync(outs, st);
     if (rc != CS_OK) return rc;
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpyAsync");
     if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");

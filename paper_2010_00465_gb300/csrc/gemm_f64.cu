@@ -18,13 +18,16 @@
 namespace cs {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8, THREADS = 256;
+constexpr int BK = 8, THREADS = 256;
 
-template <bool TX, bool TY>
+// TILE x TILE block tile (TILE = 128 or 64); thread (ty, tx) of 16 x 16 owns
+// rows {h*64 + ty*4 + i} and columns {h*64 + tx*4 + j}, h < TILE/64, i, j < 4.
+template <int TILE, bool TX, bool TY>
 __global__ void __launch_bounds__(THREADS)
 gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int64_t M, int64_t N,
                 int64_t K, int64_t ldx, int64_t ldy, int64_t ldo, int64_t bsx, int64_t bsy,
                 int64_t bse, const Epilogue<double> epi) {
+  constexpr int BM = TILE, BN = TILE, R = TILE / 16;
   __shared__ double Xs[BK][BM];
   __shared__ double Ys[BK][BN];
   const int tid = threadIdx.x;
@@ -34,11 +37,11 @@ gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int6
   X += b * bsx;
   Y += b * bsy;
 
-  double acc[8][8];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
 
   for (int64_t k0 = 0; k0 < K; k0 += BK) {
     // op(X) tile: rows m0..m0+127, columns k0..k0+7, stored k-major.
@@ -78,32 +81,29 @@ gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int6
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[8], c[8];
+      double a[R], c[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = Xs[kk][ty * 4 + i];
-        a[4 + i] = Xs[kk][64 + ty * 4 + i];
-        c[i] = Ys[kk][tx * 4 + i];
-        c[4 + i] = Ys[kk][64 + tx * 4 + i];
+      for (int i = 0; i < R; ++i) {
+        a[i] = Xs[kk][(i / 4) * 64 + ty * 4 + (i % 4)];
+        c[i] = Ys[kk][(i / 4) * 64 + tx * 4 + (i % 4)];
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], c[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], c[j], acc[i][j]);
     }
     __syncthreads();
   }
 
-  // Epilogue: this thread owns rows {ty*4+i, 64+ty*4+i} and columns
-  // {tx*4+j, 64+tx*4+j} of the block tile.
+  // Epilogue over this thread's rows and columns of the block tile.
   const int64_t eoff = b * bse;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+  for (int i = 0; i < R; ++i) {
+    const int64_t r = m0 + (i / 4) * 64 + ty * 4 + (i % 4);
     if (r >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t c = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+    for (int j = 0; j < R; ++j) {
+      const int64_t c = n0 + (j / 4) * 64 + tx * 4 + (j % 4);
       if (c >= N) continue;
       const double p = acc[i][j];
       if (epi.split_row >= 0) {
@@ -143,17 +143,28 @@ cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64
                    int64_t ldy, bool transX, bool transY, const Epilogue<double>& epi, int64_t ldo,
                    int64_t batch, int64_t bsx, int64_t bsy, int64_t bse, cudaStream_t stream) {
   if (M <= 0 || N <= 0 || batch <= 0) return CS_OK;
-  if ((M + BM - 1) / BM > 65535 || batch > 65535) return fail(CS_EINVAL, "gemm_f64: grid too large");
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)batch);
+  // 128-wide tiles unless that leaves fewer than two waves of CTAs (small
+  // batched products), where 64-wide tiles balance the SMs better.
+  const int64_t ctas128 = ((M + 127) / 128) * ((N + 127) / 128) * batch;
+  const int tile = ctas128 < 2 * 152 ? 64 : 128;
+  if ((M + tile - 1) / tile > 65535 || batch > 65535) return fail(CS_EINVAL, "gemm_f64: grid too large");
+  dim3 grid((unsigned)((N + tile - 1) / tile), (unsigned)((M + tile - 1) / tile), (unsigned)batch);
   ProfScope prof(CS_KERNEL_GEMM_F64, 2.0 * (double)M * (double)N * (double)K * (double)batch, stream);
-  if (!transX && !transY)
-    gemm_f64_kernel<false, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);
-  else if (transX && !transY)
-    gemm_f64_kernel<true, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);
-  else if (!transX && transY)
-    gemm_f64_kernel<false, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);
-  else
-    gemm_f64_kernel<true, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);
+#define CS_F64_LAUNCH(T)                                                                                           \
+  if (!transX && !transY)                                                                                          \
+    gemm_f64_kernel<T, false, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi); \
+  else if (transX && !transY)                                                                                      \
+    gemm_f64_kernel<T, true, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);  \
+  else if (!transX && transY)                                                                                      \
+    gemm_f64_kernel<T, false, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);  \
+  else                                                                                                             \
+    gemm_f64_kernel<T, true, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);
+  if (tile == 64) {
+    CS_F64_LAUNCH(64)
+  } else {
+    CS_F64_LAUNCH(128)
+  }
+#undef CS_F64_LAUNCH
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }

@@ -13,23 +13,27 @@
 // accumulator with truncation, so the error of a long accumulation grows
 // linearly with K and is biased toward zero (measured on GB300: 4e-5 relative
 // at K = 4096, against 1e-6 for an FP32 FFMA product).  The kernel therefore
-//   * accumulates X_hi Y_hi and the two correction passes in separate TMEM
-//     accumulators, so the small terms are not truncated against the large sum;
-//   * starts fresh accumulators every kGroup k-blocks (32 k) and promotes
-//     them into FP32 registers with round-to-nearest adds (two TMEM buffers
+//   * accumulates X_hi Y_hi and the correction passes in separate TMEM
+//     accumulators, so the small terms are not truncated against the large
+//     sum; the corrections (2^-11 of the main term) accumulate over the whole
+//     K, where their own truncation stays far below FP32 rounding of the sum;
+//   * starts a fresh main accumulator every kGroup k-blocks (32 k) and
+//     promotes it into Kahan-compensated FP32 register sums (two TMEM buffers
 //     ping-pong, so the tensor pipe keeps running while one is drained).
 //
 // One CTA computes a 128 x 128 tile:
 //   warp 0     TMA producer: X_hi, X_lo (128 x 32) and Y^T_hi, Y^T_lo
 //              (128 x 32) per stage into 128-byte-swizzled shared memory;
-//   warp 1     allocates 512 TMEM columns {main, corr} x 2 buffers; one lane
+//   warp 1     allocates 512 TMEM columns (main x 2 buffers, corrections); one lane
 //              issues the MMAs (cta_group::1, M = N = 128, K = 8 per
 //              instruction) and commits stages and accumulator buffers;
-//   warps 2-5  drain each accumulator buffer into registers, then run the
-//              epilogue: linear combinations, (hi, lo) split, row-major and
-//              transposed stores.
-// Measured on GB300 (n = 4096, N(0,1) operands): relative Frobenius error of
-// one product 2.4e-7, against 1.2e-6 for cuBLAS FP32 (FFMA).
+//   warps 2-9  two per TMEM lane quarter, 64 columns each: drain each main
+//              accumulator buffer into Kahan-compensated FP32 register sums
+//              (compensation terms in TMEM), then run the epilogue: linear
+//              combinations, (hi, lo) split, row-major and transposed stores.
+// Measured on GB300 (N(0,1) operands): relative Frobenius error of one
+// product 1.3e-7 at K = 256 and at K = 4096, against 2.9e-7 and 1.2e-6 for
+// cuBLAS FP32 (FFMA).
 // Every mbarrier wait is bounded; on expiry the CTA stops issuing work, waits
 // (bounded) for what it already issued, frees TMEM and raises *err.
 #include <cuda.h>
@@ -46,7 +50,13 @@ using namespace ptx;
 constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 32;  // 32 floats = 128 bytes = one swizzle row
-constexpr int kThreads = 192;
+#ifndef COSSIN_TC_EPI_WARPS
+#define COSSIN_TC_EPI_WARPS 8
+#endif
+// Epilogue warps: kEpiWarps / 4 per TMEM lane quarter, kHalf columns each.
+constexpr int kEpiWarps = COSSIN_TC_EPI_WARPS;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kHalf = BN / (kEpiWarps / 4);
 constexpr int kABytes = BM * BK * 4;
 constexpr int kBBytes = BN * BK * 4;
 constexpr int kStageBytes = 2 * (kABytes + kBBytes);
@@ -59,7 +69,7 @@ constexpr int kSmem = kStages * kStageBytes + 1024;
 #define COSSIN_TC_PASSES 4
 #endif
 constexpr int kGroup = COSSIN_TC_GROUP;  // k-blocks per accumulator buffer before promotion
-constexpr uint32_t kTmemCols = 512;    // buffer b: main at 256 b, corrections at 256 b + 128
+constexpr uint32_t kTmemCols = 512;    // main buffer b at 128 b, corrections at 256, compensation at 384
 // Instruction descriptor: D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12),
 // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t kIdesc =
@@ -75,6 +85,8 @@ __device__ __forceinline__ void split_store(float v, float* hi, float* lo, int64
   }
 }
 
+// The register file is split over 4 sub-partitions: with 10 warps (3 on two
+// of them) a thread gets at most 168 registers, with 18 warps 96.
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tf32_kernel(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
                      const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl, int M, int N,
@@ -102,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], 4);
+      mbar_init(&tempty_bar[b], kEpiWarps);
     }
     abort_flag = 0;
     kb_consumed = 0;
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d_main = tmem + 256u * b, d_corr = d_main + 128u;
+        const uint32_t d_main = tmem + 128u * b, d_corr = tmem + 256u;
         for (int kk = 0; kk < kGroup && kb < num_kb; ++kk, ++kb) {
           const int st = kb % kStages;
           if (!mbar_wait(&full_bar[st], (kb / kStages) & 1, &abort_flag)) {
@@ -164,9 +176,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t off = 32u * j;
             const uint64_t ah = desc_kmajor_sw128(a_hi + off), al = desc_kmajor_sw128(a_lo + off);
             const uint64_t bh = desc_kmajor_sw128(b_hi + off), bl = desc_kmajor_sw128(b_lo + off);
-            const uint32_t acc = (kk | j) != 0;
-            mma_tf32(d_main, ah, bh, kIdesc, acc);
-            mma_tf32(d_corr, al, bh, kIdesc, acc);
+            mma_tf32(d_main, ah, bh, kIdesc, (kk | j) != 0);  // fresh every group
+            mma_tf32(d_corr, al, bh, kIdesc, (kb | j) != 0);  // whole K
             mma_tf32(d_corr, ah, bl, kIdesc, 1);
             if (COSSIN_TC_PASSES == 4) mma_tf32(d_corr, al, bl, kIdesc, 1);
           }
@@ -178,11 +189,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int quarter = warp & 3;              // TMEM lanes 32*quarter .. +31
+    const int col0 = ((warp - 2) >> 2) * kHalf;  // this warp's kHalf columns
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    float acc[BN];
+    // Kahan-compensated running sums of the promoted main partials: the
+    // running sums stay in registers, their compensation terms in TMEM
+    // columns 384..511 (read and rewritten every group), so the sum over K
+    // adds essentially no FP32 rounding of its own.
+    float acc_hi[kHalf];
 #pragma unroll
-    for (int c = 0; c < BN; ++c) acc[c] = 0.f;
+    for (int c = 0; c < kHalf; ++c) acc_hi[c] = 0.f;
+    const uint32_t t_comp = tmem + lane_off + 384u + (uint32_t)col0;
     bool ok = true;
     for (int g = 0; g < num_groups; ++g) {
       const int b = g & 1;
@@ -199,35 +216,50 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t t_main = tmem + lane_off + 256u * b, t_corr = t_main + 128u;
+      const uint32_t t_main = tmem + lane_off + 128u * b + (uint32_t)col0;
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t vm[16], vc[16];
-        tmem_ld16(t_main + (uint32_t)c0, vm);
-        tmem_ld16(t_corr + (uint32_t)c0, vc);
+      for (int c0 = 0; c0 < kHalf; c0 += 8) {
+        uint32_t vm[8], vc[8];
+        tmem_ld8(t_main + (uint32_t)c0, vm);
+        if (g > 0) tmem_ld8(t_comp + (uint32_t)c0, vc);
         tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(vm[j]) + __uint_as_float(vc[j]);
+        for (int j = 0; j < 8; ++j) {
+          const float lo = g > 0 ? __uint_as_float(vc[j]) : 0.f;
+          const float y = __uint_as_float(vm[j]) - lo;
+          const float t = acc_hi[c0 + j] + y;
+          vc[j] = __float_as_uint((t - acc_hi[c0 + j]) - y);
+          acc_hi[c0 + j] = t;
+        }
+        tmem_st8(t_comp + (uint32_t)c0, vc);
       }
+      tmem_st_wait();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[b]);
     }
     if (ok) {
-      // The promoted sums go back to TMEM columns 0..127 (no MMA writes any
-      // buffer any more) so the epilogue can walk them in chunks.
+      // sum = main (compensated) + corrections (accumulated over the whole K
+      // in TMEM columns 256..383, complete since the last group's commit),
+      // written back to TMEM columns 0..127 so the epilogue can walk it.
+      const uint32_t t_corr = tmem + lane_off + 256u + (uint32_t)col0;
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t v[16];
+      for (int c0 = 0; c0 < kHalf; c0 += 8) {
+        uint32_t vc[8], vk[8], v[8];
+        tmem_ld8(t_corr + (uint32_t)c0, vc);
+        tmem_ld8(t_comp + (uint32_t)c0, vk);
+        tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(acc[c0 + j]);
-        tmem_st16(tmem + lane_off + (uint32_t)c0, v);
+        for (int j = 0; j < 8; ++j)
+          v[j] = __float_as_uint(acc_hi[c0 + j] + (__uint_as_float(vc[j]) - __uint_as_float(vk[j])));
+        tmem_st8(tmem + lane_off + (uint32_t)(col0 + c0), v);
       }
       tmem_st_wait();
       const int r = m0 + quarter * 32 + lane;
-      for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + lane_off + (uint32_t)c0, v);
+#pragma unroll 1
+      for (int c0 = col0; c0 < col0 + kHalf && n0 + c0 < N; c0 += 8) {
+        uint32_t v[8];
+        tmem_ld8(tmem + lane_off + (uint32_t)c0, v);
         tmem_ld_wait();
         if (r >= M) continue;
         const int cbase = n0 + c0;
@@ -236,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int rr = top ? r : r - (int)epi.split_row;
           const int t = top ? 0 : 1;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 8; ++j) {
             const int c = cbase + j;
             if (c >= N) break;
             const float val = epi.alpha[t] * __uint_as_float(v[j]) + (rr == c ? epi.gamma[t] : 0.f);
@@ -245,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 8; ++j) {
             const int c = cbase + j;
             if (c >= N) break;
             const int64_t idx = (int64_t)r * ldo + c;

@@ -90,6 +90,30 @@ __global__ void __launch_bounds__(kCols) colsum_finish(const double* __restrict_
   }
 }
 
+// ||A_b||_1 of `count` matrices of order n (contiguous, stride n^2), one
+// block per matrix: each thread sums whole columns, then a block maximum.
+__global__ void __launch_bounds__(kCols) norm1_batched_kernel(const double* __restrict__ A, int64_t n,
+                                                              double* __restrict__ out) {
+  const double* M = A + (int64_t)blockIdx.x * n * n;
+  double best = 0.0;
+  for (int64_t c = threadIdx.x; c < n; c += kCols) {
+    double sum = 0.0;
+    for (int64_t r = 0; r < n; ++r) sum += fabs(M[r * n + c]);
+    best = max_nan(best, sum);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = max_nan(best, __shfl_xor_sync(0xffffffffu, best, off));
+  __shared__ double warp_best[kCols / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_best[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = warp_best[0];
+    for (int w = 1; w < kCols / 32; ++w) b = max_nan(b, warp_best[w]);
+    out[blockIdx.x] = b;
+  }
+}
+
 template <typename T>
 cs_status norm1_impl(const T* A, int64_t n, double* partial, double* out, cudaStream_t stream) {
   if (n <= 0) {
@@ -123,6 +147,15 @@ cs_status norm1_f64(const double* A, int64_t n, double* partial, double* out, cu
 
 cs_status norm1_f32(const float* A, int64_t n, double* partial, double* out, cudaStream_t stream) {
   return norm1_impl<float>(A, n, partial, out, stream);
+}
+
+cs_status norm1_batched_f64(const double* A, int64_t n, int64_t count, double* out, cudaStream_t stream) {
+  if (count <= 0) return CS_OK;
+  if (count > 2147483647LL) return fail(CS_EINVAL, "norm1_batched: count too large");
+  ProfScope prof(CS_KERNEL_NORM1, (double)n * (double)n * sizeof(double) * (double)count, stream);
+  norm1_batched_kernel<<<(unsigned)count, kCols, 0, stream>>>(A, n, out);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
 }
 
 // ------------------------------------------------- allocation-free variant ---
