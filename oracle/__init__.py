@@ -67,6 +67,14 @@ def _load():
             lib.oracle_cossin.restype = ctypes.c_int
             lib.oracle_cossin.argtypes = [dp, ctypes.c_long, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, dp, dp, ctypes.POINTER(_Info)]
+            lib.oracle_cs.restype = ctypes.c_int
+            lib.oracle_cs.argtypes = [dp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, dp, dp, ctypes.POINTER(_Info)]
+            lib.oracle_cs_theta.restype = ctypes.c_double
+            lib.oracle_cs_theta.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.oracle_cs_select.restype = ctypes.c_int
+            lib.oracle_cs_select.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]
             lib.oracle_matmul.restype = None
             lib.oracle_matmul.argtypes = [dp, dp, dp, ctypes.c_long]
             lib.oracle_set_threads.restype = None
@@ -136,6 +144,40 @@ def cossin(A, prec: str = "double", m: int | None = None, s: int | None = None):
     if rc != 0:
         raise OracleError("oracle_cossin failed with status %d" % rc)
     return C, S, {"norm1": info.norm1, "m": info.m, "s": info.s, "products": info.products}
+
+
+CS_FAMILIES = {0: "k=3, P_{3,4}^s (2 products)", 1: "k=3, P_4^s (3 products)", 2: "k=4 (4 products)",
+               3: "k=5 (5 products)"}
+
+
+def cs(A, t: float, prec: str = "double", family: int | None = None, sigma: int | None = None):
+    """(c(t^2 A), s(t, A), info) of Sec. 2.2: cos(sqrt(t^2 A)) and
+    A^(-1/2) sin(sqrt(t^2 A)).  info["m"] is the family index 0..3 and
+    info["s"] the number of double-angle steps sigma; info["norm1"] is ||t^2 A||_1."""
+    A = _f64(A)
+    n = A.shape[0]
+    C = np.zeros((n, n), dtype=np.float64)
+    S = np.zeros((n, n), dtype=np.float64)
+    info = _Info()
+    ff = -1 if family is None else int(family)
+    fs = -1 if sigma is None else int(sigma)
+    rc = _load().oracle_cs(_ptr(A), n, float(t), PREC[prec], ff, fs, _ptr(C), _ptr(S), ctypes.byref(info))
+    if rc != 0:
+        raise OracleError("oracle_cs failed with status %d" % rc)
+    return C, S, {"norm1": info.norm1, "m": info.m, "s": info.s, "products": info.products}
+
+
+def cs_theta(prec: str, family: int) -> float:
+    return float(_load().oracle_cs_theta(PREC[prec], int(family)))
+
+
+def cs_select(normB: float, prec: str = "double"):
+    f = ctypes.c_int()
+    s = ctypes.c_int()
+    rc = _load().oracle_cs_select(float(normB), PREC[prec], ctypes.byref(f), ctypes.byref(s))
+    if rc != 0:
+        raise OracleError("oracle_cs_select failed with status %d" % rc)
+    return f.value, s.value
 
 
 def matmul(X, Y) -> np.ndarray:

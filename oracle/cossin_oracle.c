@@ -406,5 +406,257 @@ done:
   return rc;
 }
 
+/* ------------------------------------------------------------------------
+ * Sec. 2.2: c(t^2 A) = cos(sqrt(t^2 A)) and s(t, A) = A^(-1/2) sin(sqrt(t^2 A))
+ * together, evaluated on B = t^2 A directly (the schemes of Sec. 2.1 with
+ * A_2 replaced by B and the last sine product replaced by the scalar t), and
+ * recovered with c(4 t^2 A) = 2 c^2 - I, s(2t, A) = 2 s c (Sec. 1).
+ *
+ * Families (products):  0 = k=3 with P_{3,4}^s (2),  1 = k=3 with P_4^s (3),
+ *                       2 = k=4 (4),                   3 = k=5 (5).
+ * Reading of eq. Algorithm83eA for P_{3,4}^s: the printed "- (6!/7!) B_4"
+ * has the wrong sign; B_4 already carries -1/6!, and only "+" reproduces the
+ * series through B^3 (as in eq. Algorithm4sA).
+ * The paper gives no admissible norms for these schemes.  THETA_CS holds the
+ * largest ||B||_1 at which the Sec. 3 error series (150 terms) of the cosine
+ * part, and of the sine part divided by t, stay <= u; it is the smaller of the
+ * two (the cosine values are theta_2m^2 of Tables 1-2).
+ * ---------------------------------------------------------------------- */
+static const double THETA_CS[2][4] = {
+    {3.44587e-3, 1.32137e-2, 9.62511e-1, 3.64043},
+    {5.22375e-1, 7.35401e-1, 8.96121, 21.8484},
+};
+static const int PI_CS[4] = {2, 3, 4, 5};
+
+double oracle_cs_theta(int prec, int family) {
+  if (prec < 0 || prec > 1 || family < 0 || family > 3) return -1.0;
+  return THETA_CS[prec][family];
+}
+
+/* (family, sigma) of minimal cost Pi + 2 sigma with ||B||_1 / 4^sigma <= theta. */
+int oracle_cs_select(double normB, int prec, int* f_out, int* s_out) {
+  if (prec < 0 || prec > 1) return ORC_EINVAL;
+  if (!isfinite(normB)) return ORC_ENONFINITE;
+  int best = -1, best_s = 0, best_cost = 1 << 30;
+  for (int f = 0; f < 4; ++f) {
+    int sg = 0;
+    while (ldexp(normB, -2 * sg) > THETA_CS[prec][f]) ++sg;
+    if (sg > ORC_MAX_S) continue;
+    const int cost = PI_CS[f] + 2 * sg;
+    if (cost < best_cost || (cost == best_cost && sg < best_s)) {
+      best_cost = cost;
+      best = f;
+      best_s = sg;
+    }
+  }
+  if (best < 0) return ORC_ERANGE;
+  *f_out = best;
+  *s_out = best_s;
+  return ORC_OK;
+}
+
+/* k = 3 products: eq. Algorithm83eA (P_4^c) with P_{3,4}^s or P_4^s. */
+static int cs_k3(const double* B, double t, long n, int with_p4s, double* C, double* S) {
+  int rc = ORC_OK;
+  double *B2 = NULL, *R = NULL, *B4 = NULL, *T = NULL;
+  NEWMAT(B2); NEWMAT(R); NEWMAT(B4); NEWMAT(T);
+  matmul(B, B, B2, n);                                       /* B_2 = B^2 */
+  {
+    const double c[2] = {-1.0 / 720.0, 1.0 / 40320.0};       /* -B/6! + B_2/8! */
+    const double* M[2] = {B, B2};
+    lincomb(R, n, 0.0, 2, c, M);
+  }
+  matmul(B2, R, B4, n);                                      /* B_4 */
+  {
+    const double c[3] = {-1.0 / 2.0, 1.0 / 24.0, 1.0};
+    const double* M[3] = {B, B2, B4};
+    lincomb(C, n, 1.0, 3, c, M);                             /* P_4^c */
+  }
+  if (!with_p4s) {
+    const double c[3] = {-t / 6.0, t / 120.0, t * 720.0 / 5040.0};
+    const double* M[3] = {B, B2, B4};
+    lincomb(S, n, t, 3, c, M);                               /* P_{3,4}^s, "+" (6!/7!) B_4 */
+  } else {
+    const double c[2] = {-1.0 / 5040.0, 1.0 / 362880.0};     /* -B/7! + B_2/9! */
+    const double* M[2] = {B, B2};
+    lincomb(R, n, 0.0, 2, c, M);
+    matmul(B2, R, T, n);
+    const double c2[3] = {-t / 6.0, t / 120.0, t};
+    const double* M2[3] = {B, B2, T};
+    lincomb(S, n, t, 3, c2, M2);                             /* P_4^s */
+  }
+done:
+  free(B2); free(R); free(B4); free(T);
+  return rc;
+}
+
+/* k = 4 products: P_8^c with the coefficients of eq. cosm8 (y0 = 1,
+ * y1 = -1/2, y2 = x8) and P_{8,12}^s with the z list of Sec. 2.1, k = 6. */
+static int cs_k4(const double* B, double t, long n, double* C, double* S) {
+  int rc = ORC_OK;
+  double *B2 = NULL, *R = NULL, *B4 = NULL, *L = NULL, *Wm = NULL, *B8 = NULL, *C12 = NULL;
+  const double r = sqrt(36681.0);
+  const double x1 = 7.0 / 500.0, x2 = -7.0 / 60000.0, x3 = (-1533.0 + 7.0 * r) / 2500.0;
+  const double x4 = -5.0 * (124581.0 + 391.0 * r) / 10594584.0, x5 = 9775.0 / 10594584.0;
+  const double x6 = -5.0 * (1001.0 + r) / 508540032.0, x7 = 3125.0 / 889945056.0;
+  const double x8 = (1549211.0 + 3246.0 * r) / 63063000.0;
+  const double z0 = 8887.0 / 4794.0, z1 = -1897.0 / 3196.0, z2 = 25259.0 / 575280.0;
+  const double z3 = -965093875.0 / 9674368704.0, z4 = -4093.0 / 4794.0;
+  const double z5 = 25698275.0 / 29023106112.0, z6 = -3907675.0 / 348277273344.0;
+  const double z7 = 11865625.0 / 3656911370112.0, z8 = 25.0 / 308756448.0;
+  NEWMAT(B2); NEWMAT(R); NEWMAT(B4); NEWMAT(L); NEWMAT(Wm); NEWMAT(B8); NEWMAT(C12);
+  matmul(B, B, B2, n);
+  {
+    const double c[2] = {x1, x2};
+    const double* M[2] = {B, B2};
+    lincomb(R, n, 0.0, 2, c, M);
+  }
+  matmul(B2, R, B4, n);                                      /* B_4 = B_2 (x1 B + x2 B_2) */
+  {
+    const double c[2] = {x3, 1.0};
+    const double* M[2] = {B2, B4};
+    lincomb(L, n, 0.0, 2, c, M);
+  }
+  {
+    const double c[3] = {x5, x6, x7};
+    const double* M[3] = {B, B2, B4};
+    lincomb(Wm, n, x4, 3, c, M);
+  }
+  matmul(L, Wm, B8, n);                                      /* B_8 */
+  {
+    const double c[3] = {-0.5, x8, 1.0};
+    const double* M[3] = {B, B2, B8};
+    lincomb(C, n, 1.0, 3, c, M);                             /* P_8^c */
+  }
+  {
+    const double c[4] = {z5, z6, z7, z8};
+    const double* M[4] = {B, B2, B4, C};
+    lincomb(Wm, n, z5, 4, c, M);
+  }
+  matmul(Wm, B4, C12, n);                                    /* C_12 */
+  {
+    const double c[5] = {t * z1, t * z2, t * z3, t * z4, t};
+    const double* M[5] = {B, B2, B4, C, C12};
+    lincomb(S, n, t * z0, 5, c, M);                          /* P_{8,12}^s */
+  }
+done:
+  free(B2); free(R); free(B4); free(L); free(Wm); free(B8); free(C12);
+  return rc;
+}
+
+/* k = 5 products: eq. poly12 (P_12^c) with Coefs7cA and P_{11,24}^s with
+ * Coefs7sA (its P_12^c(A) read as P_12^c(B)). */
+static int cs_k5(const double* B, double t, long n, double* C, double* S) {
+  int rc = ORC_OK;
+  static const double a[4][4] = {
+      {0.0, 0.55751443809990408029, 0.75936877868464999248, 0.0},
+      {0.0, -0.61577924683458386455, -0.01560333979813817129, -0.039649968743474473091},
+      {0.02264979811206039519, 0.00747198841446687051, 0.00010936989591908396,
+       0.000155490073503821463},
+      {-0.00013110924142135755, -0.00003362444420476012, -1.03893360877457159499e-6,
+       -1.126739663071170022488e-6},
+  };
+  static const double z[12] = {
+      0.10090808375109885598,  -0.07668753546445299316, 0.00084924846993243257,
+      -0.00001220406904464391, 0.98499703159318860027,  -0.84925233648155398756,
+      1.0,                     0.00095544138280925799,  4.56337109377154270633e-6,
+      2.73461259403000427141e-8, 0.00048550288474842477, -4.15891109384923342531e-7,
+  };
+  double *B2 = NULL, *B3 = NULL, *D[4] = {NULL, NULL, NULL, NULL}, *B6 = NULL, *L = NULL, *P = NULL,
+         *Wm = NULL, *C24 = NULL;
+  NEWMAT(B2); NEWMAT(B3);
+  for (int j = 0; j < 4; ++j) NEWMAT(D[j]);
+  NEWMAT(B6); NEWMAT(L); NEWMAT(P); NEWMAT(Wm); NEWMAT(C24);
+  matmul(B, B, B2, n);
+  matmul(B2, B, B3, n);
+  for (int j = 0; j < 4; ++j) {
+    const double c[3] = {a[1][j], a[2][j], a[3][j]};
+    const double* M[3] = {B, B2, B3};
+    lincomb(D[j], n, a[0][j], 3, c, M);                      /* D_1 .. D_4 */
+  }
+  matmul(D[3], D[3], B6, n);
+  {
+    const double c[2] = {1.0, 1.0};
+    const double* M[2] = {D[2], B6};
+    lincomb(B6, n, 0.0, 2, c, M);                            /* B_6 = D_3 + D_4^2 */
+  }
+  {
+    const double c[2] = {1.0, 1.0};
+    const double* M[2] = {D[1], B6};
+    lincomb(L, n, 0.0, 2, c, M);
+  }
+  matmul(L, B6, P, n);
+  {
+    const double c[2] = {1.0, 1.0};
+    const double* M[2] = {D[0], P};
+    lincomb(C, n, 0.0, 2, c, M);                             /* P_12^c */
+  }
+  {
+    const double c[5] = {z[7], z[8], z[9], z[10], z[11]};
+    const double* M[5] = {B, B2, B3, B6, C};
+    lincomb(Wm, n, z[6], 5, c, M);
+  }
+  matmul(Wm, C, C24, n);                                     /* C_24 */
+  {
+    const double c[6] = {t * z[1], t * z[2], t * z[3], t * z[4], t * z[5], t};
+    const double* M[6] = {B, B2, B3, B6, C, C24};
+    lincomb(S, n, t * z[0], 6, c, M);                        /* P_{11,24}^s */
+  }
+done:
+  free(B2); free(B3);
+  for (int j = 0; j < 4; ++j) free(D[j]);
+  free(B6); free(L); free(P); free(Wm); free(C24);
+  return rc;
+}
+
+/* C = c(t^2 A), S = s(t, A).  force_family / force_sigma as force_m / force_s. */
+int oracle_cs(const double* A, long n, double t, int prec, int force_family, int force_sigma, double* C,
+              double* S, oracle_info* info) {
+  if (n < 0 || prec < 0 || prec > 1 || !isfinite(t)) return ORC_EINVAL;
+  if (force_family < -1 || force_family > 3) return ORC_EINVAL;
+  if (force_sigma < -1 || force_sigma > ORC_MAX_S) return ORC_EINVAL;
+  if ((force_family == -1) != (force_sigma == -1)) return ORC_EINVAL;
+  const double normB = t * t * oracle_norm1(A, n);
+  int f, sg, rc = ORC_OK;
+  if (!isfinite(normB)) return ORC_ENONFINITE;
+  if (force_family == -1) {
+    rc = oracle_cs_select(normB, prec, &f, &sg);
+    if (rc != ORC_OK) return rc;
+  } else {
+    f = force_family;
+    sg = force_sigma;
+  }
+  if (info) {
+    info->norm1 = normB;
+    info->m = f;
+    info->s = sg;
+    info->products = PI_CS[f] + 2 * sg;
+  }
+  if (n == 0) return ORC_OK;
+  const double ts = ldexp(t, -sg);                           /* t / 2^sigma */
+  double *Bs = NULL, *C2 = NULL, *T = NULL;
+  NEWMAT(Bs); NEWMAT(C2); NEWMAT(T);
+  scale(Bs, A, ts * ts, n);                                  /* B = (t/2^sigma)^2 A */
+  switch (f) {
+    case 0: rc = cs_k3(Bs, ts, n, 0, C, S); break;
+    case 1: rc = cs_k3(Bs, ts, n, 1, C, S); break;
+    case 2: rc = cs_k4(Bs, ts, n, C, S); break;
+    default: rc = cs_k5(Bs, ts, n, C, S); break;
+  }
+  if (rc != ORC_OK) goto done;
+  for (int j = 0; j < sg; ++j) {                             /* c(4t^2A) = 2c^2 - I, s(2t,A) = 2sc */
+    matmul(C, C, C2, n);
+    matmul(S, C, T, n);
+    for (long i = 0; i < n; ++i)
+      for (long k = 0; k < n; ++k) {
+        C[i * n + k] = 2.0 * C2[i * n + k] - ((i == k) ? 1.0 : 0.0);
+        S[i * n + k] = 2.0 * T[i * n + k];
+      }
+  }
+done:
+  free(Bs); free(C2); free(T);
+  return rc;
+}
+
 /* Plain matrix product, exposed so that tests can assemble identities. */
 void oracle_matmul(const double* X, const double* Y, double* Z, long n) { matmul(X, Y, Z, n); }

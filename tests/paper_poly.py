@@ -183,3 +183,45 @@ def theta(poly, sine: bool, u, nterms: int = 150):
         else:
             lo = mid
     return lo
+
+
+# ------------------------------------------------------------- Sec. 2.2 ---
+# The c(t^2 A), s(t, A) schemes are the Sec. 2.1 polynomials with A_2 = A^2
+# replaced by B = t^2 A and the leading factor A of the sine replaced by t:
+# their coefficients in B are the even coefficients of the cosine polynomial
+# and the odd coefficients of the sine polynomial of the Sec. 2.1 scheme.
+CS_SCHEMES = {0: ("c8", "s79"), 1: ("c8", "s9"), 2: ("c16", "s17"), 3: ("c24", "s23")}
+
+
+def cs_coefficients(family: int, refined: bool = False):
+    polys = schemes(refined=refined)
+    ck, sk = CS_SCHEMES[family]
+    pc, ps = polys[ck], polys[sk]
+    cos_b = [pc[2 * k] if 2 * k < len(pc) else mp.mpf(0) for k in range(len(pc) // 2 + 1)]
+    sin_b = [ps[2 * k + 1] if 2 * k + 1 < len(ps) else mp.mpf(0) for k in range(len(ps) // 2 + 1)]
+    return cos_b, sin_b
+
+
+def cos_b_taylor(k: int):
+    return mp.mpf(-1) ** k / mp.factorial(2 * k)
+
+
+def sin_b_taylor(k: int):
+    return mp.mpf(-1) ** k / mp.factorial(2 * k + 1)
+
+
+def theta_b(coef, target, u, nterms: int = 150):
+    """Largest ||B|| with sum_k |target_k - coef_k| ||B||^k <= u (150 terms)."""
+    c = []
+    for k in range(nterms + 1):
+        ck = coef[k] if k < len(coef) else mp.mpf(0)
+        a = abs(target(k) - ck)
+        c.append(a if a > mp.mpf(10) ** -45 else mp.mpf(0))
+    lo, hi = mp.mpf(0), mp.mpf(400)
+    for _ in range(160):
+        mid = (lo + hi) / 2
+        if sum(ci * mid ** k for k, ci in enumerate(c)) > u:
+            hi = mid
+        else:
+            lo = mid
+    return lo
