@@ -346,7 +346,42 @@ def forms(api, wsp):
         row["split_speedup_vs_fp64_path"] = row["fp64"]["ms"] / row["split_tf32"]["ms"]
         out["norm%g" % nrm] = row
     return {"n": N, "family": "normal", "split_tf32": out, "batched": batched_form(api),
-            "adjoint": adjoint_form(api)}
+            "adjoint": adjoint_form(api), "cs": cs_form(api, wsp)}
+
+
+def cs_form(api, wsp):
+    """The Sec. 2.2 variant at n = 4096: c(t^2 A), s(t, A) of A = X^2 (t = 1)
+    against cos(X), sin(X) of the cos/sin path, both timed with CUDA events;
+    the variant starts from B = A and drops the sine's last product."""
+    import torch
+    from paper_2010_00465_gb300 import inputs
+    out = {}
+    for nrm in (1.0, 8.0):
+        X = torch.from_numpy(inputs.matrix(N, "normal", nrm, index=4)).cuda()
+        A = X @ X
+        for prec in ("fp64", "split_tf32"):
+            need = api.workspace_size(N, prec)
+            ws = wsp if wsp.numel() >= need else torch.empty(need, dtype=torch.uint8, device="cuda")
+            row = {}
+            res = {}
+            for name, call in (("cossin", lambda: api.cossin(X, prec, workspace=ws, return_info=True)),
+                               ("cs", lambda: api.cossin_cs(A, 1.0, prec, workspace=ws, return_info=True))):
+                call()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                C, S, info = call()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                res[name] = C
+                row[name] = {"ms": ms, "m": info["m"], "s": info["s"], "products": info["products"],
+                             "alg_tflops": info["flops"] / ms / 1e9}
+            row["rel_diff_c_vs_cos"] = float((res["cs"] - res["cossin"]).norm() / res["cossin"].norm())
+            row["speedup_vs_cossin"] = row["cossin"]["ms"] / row["cs"]["ms"]
+            out["normX%g_%s" % (nrm, prec)] = row
+    return out
 
 
 def adjoint_form(api, count=512, n=128, reps=3):

@@ -126,8 +126,33 @@ cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, voi
                     void* ws_dev, size_t ws_bytes, int32_t force_m, int32_t force_s,
                     cs_info* info, cossin_stream_t stream);
 
+/* The Sec. 2.2 variant: C = c(t^2 A) = cos(sqrt(t^2 A)) and
+ * S = s(t, A) = A^(-1/2) sin(sqrt(t^2 A)) (each a power series in t^2 A, so
+ * no square root is formed), the functions that advance u'' + A u = 0 by a
+ * step t.  The schemes of Sec. 2.1 run on B = (t / 2^sigma)^2 A with the
+ * first product (A^2) and the sine's last product (A times ...) removed, so
+ * the four families cost 2, 3, 4 and 5 products; sigma double-angle steps
+ * C <- 2C^2 - I, S <- 2SC follow.  The family and sigma minimise products +
+ * 2 sigma subject to ||B||_1 <= theta_cs (the paper prints no admissible
+ * norms for these schemes: the library's values come from the Sec. 3 error
+ * series of the scalar polynomials in B; ties go to the smaller sigma).
+ *   family 0: k = 3 with P_{3,4}^s (the minus sign printed before the
+ *             (6!/7!) B_4 term is read as plus), 2 products;
+ *   family 1: k = 3 with P_4^s, 3 products;
+ *   family 2: k = 4 (P_8^c, P_{8,12}^s on B), 4 products;
+ *   family 3: k = 5 (P_12^c, P_{11,24}^s on B), 5 products.
+ * Arguments as cossin_ex (same workspace size), plus the finite step t;
+ * force_family in [0, 3] with force_sigma in [0, 64], or both -1.  info->m
+ * holds the family, info->s sigma and info->norm1 ||t^2 A||_1.
+ * CS_ENONFINITE if t^2 ||A||_1 is not finite, CS_ERANGE if sigma would
+ * exceed 64, CS_EINVAL for a non-finite t or bad arguments.  ws_dev may be
+ * NULL, in which case the workspace is allocated on `stream` as in cossin. */
+cs_status cossin_cs(const void* A_dev, int64_t n, double t, cs_prec prec, void* C_dev, void* S_dev,
+                    void* ws_dev, size_t ws_bytes, int32_t force_family, int32_t force_sigma,
+                    cs_info* info, cossin_stream_t stream);
+
 /* One product P = X Y (n x n, row-major) on the library's product kernel for
- * `prec`: the FP64 kernel for CS_FP64, the three-pass TF32 tensor-core kernel
+ * `prec`: the FP64 kernel for CS_FP64, the four-pass TF32 tensor-core kernel
  * for CS_FP32 (FP32 in and out) and CS_SPLIT_TF32 (FP64 in and out, computed
  * from the FP32 roundings of X and Y).  These are the products the method
  * counts (Pi_2m in Tables 1-2).  P must not overlap X or Y.  Allocates and

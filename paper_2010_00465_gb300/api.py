@@ -104,6 +104,42 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
     return C, S
 
 
+def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None, sigma: int | None = None,
+              workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
+    """c(t^2 A) = cos(sqrt(t^2 A)) and s(t, A) = A^(-1/2) sin(sqrt(t^2 A)) (Sec. 2.2).
+
+    ``family`` (0..3: 2, 3, 4 or 5 products) and ``sigma`` (double-angle
+    steps) force the scheme; info["m"] is the family, info["norm1"] ||t^2 A||_1.
+    """
+    p = _prec(prec, A)
+    host = not A.is_cuda
+    if host:
+        A = A.to("cuda", non_blocking=True)
+    A = A.contiguous()
+    n = _check_matrix(A, p)
+    if out is None:
+        C = torch.empty_like(A)
+        S = torch.empty_like(A)
+    else:
+        C, S = out
+    need = workspace_size(n, p)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
+    info = CsInfo()
+    ff = -1 if family is None else int(family)
+    fs = -1 if sigma is None else int(sigma)
+    check(lib().cossin_cs(ctypes.c_void_p(A.data_ptr()), n, float(t), p, ctypes.c_void_p(C.data_ptr()),
+                          ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
+                          workspace.numel() * workspace.element_size(), ff, fs, ctypes.byref(info),
+                          _stream_ptr(stream)))
+    if host:
+        C = C.cpu()
+        S = S.cpu()
+    if return_info:
+        return C, S, info.as_dict()
+    return C, S
+
+
 def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Tensor:
     """P = X Y on the library's product kernel for ``prec``."""
     p = _prec(prec, X)

@@ -229,6 +229,65 @@ std::vector<Step> chain_plan(int m, int s) {
   return P;
 }
 
+// ------------------------------------------------------------------ specs ---
+PlanSpec cossin_spec(int m, int s) {
+  PlanSpec P;
+  P.steps = chain_plan(m, s);
+  P.s = s;
+  return P;
+}
+
+int cs_products(int family) { return cs_family_products(family); }
+
+// Sec. 2.2: the schemes of Sec. 2.1 evaluated on B = t^2 A directly.  B takes
+// the place of A_2 (slot W0, written scaled before the steps, so the first
+// product A A disappears) and the sine's last product A (...) becomes the
+// scalar t: the output that fed it is written to S scaled by t / 2^sigma.
+// Family 0 is the k = 4 chain (P_4^c with P_{3,4}^s, whose printed minus
+// sign in front of (6!/7!) B_4 is read as plus); family 1 adds the product
+// B_2 (-B/7! + B_2/9!) for P_4^s; families 2 and 3 are the k = 6 and k = 7
+// chains (P_8^c, P_{8,12}^s and P_12^c, P_{11,24}^s).
+PlanSpec cs_spec(int family, int sigma, double t) {
+  const double ts = ldexp(t, -sigma);
+  PlanSpec P;
+  P.s = sigma;
+  P.scale_into_w0 = true;
+  P.input_scale = ts * ts;
+  if (family == 1) {
+    auto out = [](int slot, double alpha, double gamma, std::vector<std::pair<int, double>> beta = {}) {
+      return OutSpec{slot, alpha, gamma, std::move(beta), {}};
+    };
+    P.steps.push_back(Step{W(0), W(0), {out(W(1), 1.0, 0.0),                                   // B_2
+                                        out(W(2), 1.0 / 40320, 0.0, {{W(0), -1.0 / 720}}),     // -B/6! + B_2/8!
+                                        out(W(3), 1.0 / 24, 1.0, {{W(0), -0.5}}),              // I - B/2! + B_2/4!
+                                        out(W(4), 1.0 / 362880, 0.0, {{W(0), -1.0 / 5040}}),   // -B/7! + B_2/9!
+                                        out(W(5), 1.0 / 120, 1.0, {{W(0), -1.0 / 6}})}});      // I - B/3! + B_2/5!
+    P.steps.push_back(Step{W(1), W(2), {out(SL_C, 1.0, 0.0, {{W(3), 1.0}})}});                 // P_4^c
+    P.steps.push_back(Step{W(1), W(4), {out(SL_S, ts, 0.0, {{W(5), ts}})}});                   // P_4^s
+    return P;
+  }
+  const int m = family == 0 ? 8 : family == 2 ? 16 : 24;
+  std::vector<Step> full = chain_plan(m, 0);
+  // drop A_2 = A A (W0 holds B) and the final S = A (...)
+  const Step last = full.back();
+  P.steps.assign(full.begin() + 1, full.end() - 1);
+  const int q = last.Y;  // the sine's right factor
+  for (auto it = P.steps.rbegin(); it != P.steps.rend(); ++it) {
+    bool found = false;
+    for (OutSpec& o : it->outs) {
+      if (o.slot != q) continue;
+      o.slot = SL_S;
+      o.alpha *= ts;
+      o.gamma *= ts;
+      for (auto& b : o.beta) b.second *= ts;
+      for (auto& d : o.delta) d.second *= ts;
+      found = true;
+    }
+    if (found) break;
+  }
+  return P;
+}
+
 // -------------------------------------------------------------- execution ---
 namespace {
 
@@ -254,16 +313,18 @@ Epilogue<T> build_epilogue(const Step& st, T* const* hi, T* const* lo) {
   return b.e;
 }
 
-cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, const Layout& L, int m,
-                  int s, cudaStream_t stream) {
+cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, const Layout& L, const PlanSpec& P,
+                  cudaStream_t stream) {
   double* slot[SL_COUNT] = {};
   double* ping[2] = {(double*)(ws + L.ping64[0]), (double*)(ws + L.ping64[1])};
   const size_t n2 = (size_t)n * (size_t)n;
+  const int s = P.s;
   slot[SL_A] = const_cast<double*>(A);
   slot[SL_C] = s == 0 ? C : ping[0];
   slot[SL_S] = s == 0 ? S : ping[0] + n2;
   for (int w = 0; w < kWorkSlots; ++w) slot[W(w)] = (double*)(ws + L.w[w]);
-  for (const Step& st : chain_plan(m, s)) {
+  if (P.scale_into_w0) CS_CHECK(scale_f64(A, slot[W(0)], (int64_t)n2, P.input_scale, stream));
+  for (const Step& st : P.steps) {
     Epilogue<double> e = build_epilogue<double>(st, slot, nullptr);
     CS_CHECK(gemm_f64(slot[st.X], slot[st.Y], n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, stream));
   }
@@ -341,7 +402,7 @@ namespace {
 }  // namespace
 
 cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* ws, const Layout& L,
-                   int m, int s, cudaStream_t stream);
+                   const PlanSpec& P, cudaStream_t stream);
 cs_status matmul_tf32(const void* X, const void* Y, int64_t n, bool f64_io, void* P, cudaStream_t stream);
 
 cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
@@ -381,8 +442,56 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   }
   const int prods = products_of(m) + 2 * s;
   if (info) *info = cs_info{nrm, m, s, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
-  if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, m, s, stream);
-  return run_tf32(A, n, prec, C, S, w, L, m, s, stream);
+  const PlanSpec spec = cossin_spec(m, s);
+  if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, stream);
+  return run_tf32(A, n, prec, C, S, w, L, spec, stream);
+}
+
+// c(t^2 A), s(t, A) of Sec. 2.2 (see cs_spec); info->m is the family index.
+cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
+                  int32_t force_f, int32_t force_s, cs_info* info, cudaStream_t stream) {
+  CS_CHECK(check_prec(prec));
+  if (n < 0 || n > kMaxN) return fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (!isfinite(t)) return fail(CS_EINVAL, "t must be finite");
+  if ((force_f == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_family and force_sigma must both be -1 or both set");
+  if (force_f < -1 || force_f > 3) return fail(CS_EINVAL, "force_family must be in [0, 3]");
+  if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_sigma must be in [0, 64]");
+  const int table = prec == CS_FP64 ? 0 : 1;
+  if (n == 0) {
+    if (info) *info = cs_info{0.0, force_f == -1 ? 0 : force_f, force_s == -1 ? 0 : force_s, 0, table, 0.0};
+    return CS_OK;
+  }
+  if (!A || !C || !S) return fail(CS_EINVAL, "null matrix pointer");
+  const size_t bytes = (size_t)n * (size_t)n * elem_size(prec);
+  if (overlaps(A, bytes, C, bytes) || overlaps(A, bytes, S, bytes) || overlaps(C, bytes, S, bytes))
+    return fail(CS_EINVAL, "A, C and S must not overlap");
+  const Layout L = make_layout(n, prec);
+  if (!ws || ws_bytes < L.total) return fail(CS_EINVAL, "workspace missing or too small");
+  if (((uintptr_t)ws & 255) != 0) return fail(CS_EINVAL, "workspace must be 256-byte aligned");
+  char* w = (char*)ws;
+  double* nrm_dev = (double*)(w + L.norm_out);
+  if (prec == CS_FP32)
+    CS_CHECK(norm1_f32((const float*)A, n, (double*)(w + L.norm_partial), nrm_dev, stream));
+  else
+    CS_CHECK(norm1_f64((const double*)A, n, (double*)(w + L.norm_partial), nrm_dev, stream));
+  double nrm = 0.0;
+  CS_CHECK(read_norm(nrm_dev, &nrm, stream));
+  const double normB = t * t * nrm;
+  if (!isfinite(normB)) return fail(CS_ENONFINITE, "||t^2 A||_1 is not finite");
+  int f, sg;
+  if (force_f == -1) {
+    const int rc = select_cs_family(normB, table, &f, &sg);
+    if (rc == 3) return fail(CS_ENONFINITE, "||t^2 A||_1 is not finite");
+    if (rc == 4) return fail(CS_ERANGE, "||t^2 A||_1 needs more than 64 double-angle steps");
+  } else {
+    f = force_f;
+    sg = force_s;
+  }
+  const int prods = cs_family_products(f) + 2 * sg;
+  if (info) *info = cs_info{normB, f, sg, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
+  const PlanSpec spec = cs_spec(f, sg, t);
+  if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, stream);
+  return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
 
 }  // namespace cs
@@ -468,6 +577,25 @@ cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, v
     return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
   }
   return cs::matmul_tf32(X, Y, n, prec == CS_SPLIT_TF32, P, st);
+}
+
+cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
+                    int32_t force_family, int32_t force_sigma, cs_info* info, cossin_stream_t stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ws) return cs::cs_impl(A, n, t, prec, C, S, ws, ws_bytes, force_family, force_sigma, info, st);
+  CS_CHECK(cs::check_prec(prec));
+  if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (n == 0) return cs::cs_impl(A, n, t, prec, C, S, nullptr, 0, force_family, force_sigma, info, st);
+  const size_t bytes = cs::make_layout(n, prec).total;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cs::fail(CS_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  cs_status rc = cs::cs_impl(A, n, t, prec, C, S, buf, bytes, force_family, force_sigma, info, st);
+  cudaFreeAsync(buf, st);
+  return rc;
 }
 
 const char* cossin_last_error(void) { return cs::g_last_error.c_str(); }

@@ -109,6 +109,9 @@ cs_status norm1_f32(const float* A, int64_t n, double* partial_dev, double* out_
 // ||A_b||_1 for `count` contiguous FP64 matrices of order n, one block each.
 cs_status norm1_batched_f64(const double* A, int64_t n, int64_t count, double* out, cudaStream_t stream);
 
+// dst[i] = scale * src[i], i < count (FP64).
+cs_status scale_f64(const double* src, double* dst, int64_t count, double scale, cudaStream_t stream);
+
 // Host selection (step 2).
 cs_status select_ms(double norm1, int table, int* m, int* s);
 int products_of(int m);

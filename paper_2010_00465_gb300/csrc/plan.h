@@ -35,6 +35,21 @@ struct Step {
 
 std::vector<Step> chain_plan(int m, int s);
 
+// What an executor runs: the product steps, then s double-angle steps.  With
+// scale_into_w0 the input is first copied into W0 scaled by input_scale (the
+// c(t^2 A), s(t, A) variant starts from B = (t / 2^s)^2 A there).
+struct PlanSpec {
+  std::vector<Step> steps;
+  int s = 0;
+  bool scale_into_w0 = false;
+  double input_scale = 1.0;
+};
+
+PlanSpec cossin_spec(int m, int s);
+// family 0: k = 3 with P_{3,4}^s, 1: k = 3 with P_4^s, 2: k = 4, 3: k = 5 (Sec. 2.2)
+PlanSpec cs_spec(int family, int sigma, double t);
+int cs_products(int family);
+
 // Byte offsets into the caller's workspace.
 //  FP64:       w[8] (n x n doubles), ping64[2] (stacked [C; S], 2n x n doubles)
 //  TF32 modes: every slot is four n x ld32 float arrays {hi, lo, hi^T, lo^T}

@@ -44,12 +44,13 @@ struct TcEpilogue {
 cs_status gemm_tf32(const TcOperand& X, const TcOperand& YT, int64_t M, int64_t N, int64_t K, int64_t ldo,
                     const TcEpilogue& epi, int* err, int bn, cudaStream_t stream);
 
-// (hi, lo) split of an n x n row-major matrix (FP32 or FP64 source, leading
-// dimension n) into padded (ld) hi/lo and, if hiT is non-null, the transposed split.
+// (hi, lo) split of scale * (an n x n row-major matrix, FP32 or FP64 source,
+// leading dimension n) into padded (ld) hi/lo and, if hiT is non-null, the
+// transposed split.  The scaled value is rounded to FP32 once.
 cs_status split_f32(const float* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                    cudaStream_t stream);
+                    cudaStream_t stream, double scale = 1.0);
 cs_status split_f64(const double* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                    cudaStream_t stream);
+                    cudaStream_t stream, double scale = 1.0);
 
 // dst (n x n, leading dimension n) = hi + lo (padded ld), as FP32 or FP64.
 cs_status combine_f32(const float* hi, const float* lo, int64_t n, int64_t ld, float* dst, cudaStream_t stream);

@@ -42,8 +42,9 @@ bool needs_transpose(const std::vector<Step>& plan, size_t i, int slot, bool squ
 
 }  // namespace
 
-cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* ws, const Layout& L, int m,
-                   int s, cudaStream_t stream) {
+cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* ws, const Layout& L,
+                   const PlanSpec& spec, cudaStream_t stream) {
+  const int s = spec.s;
   const int64_t ld = L.ld32;
   auto F = [&](size_t off) { return (float*)(ws + off); };
   TcSlot slot[SL_COUNT];
@@ -57,13 +58,15 @@ cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, cha
   if (!err) return fail(CS_ECUDA, "cannot resolve the device error word");
   const int bn = tile_bn(n);
 
+  // The input goes to SL_A, or scaled to W0 for the c(t^2 A), s(t, A) variant.
+  const TcSlot& in = spec.scale_into_w0 ? slot[W(0)] : slot[SL_A];
   if (prec == CS_FP32)
-    CS_CHECK(split_f32((const float*)A, n, ld, slot[SL_A].hi, slot[SL_A].lo, slot[SL_A].hiT, slot[SL_A].loT, stream));
+    CS_CHECK(split_f32((const float*)A, n, ld, in.hi, in.lo, in.hiT, in.loT, stream, spec.input_scale));
   else
-    CS_CHECK(split_f64((const double*)A, n, ld, slot[SL_A].hi, slot[SL_A].lo, slot[SL_A].hiT, slot[SL_A].loT, stream));
+    CS_CHECK(split_f64((const double*)A, n, ld, in.hi, in.lo, in.hiT, in.loT, stream, spec.input_scale));
 
   const bool tc_squaring = (prec == CS_FP32) && s > 0;
-  const std::vector<Step> plan = chain_plan(m, s);
+  const std::vector<Step>& plan = spec.steps;
   for (size_t i = 0; i < plan.size(); ++i) {
     const Step& st = plan[i];
     TcEpilogue e;

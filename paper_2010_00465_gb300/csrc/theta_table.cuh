@@ -49,4 +49,36 @@ __host__ __device__ inline int select_family(double norm, int table, int* f_out,
   return 0;
 }
 
+// Sec. 2.2 schemes on B = t^2 A (families: k = 3 with P_{3,4}^s, k = 3 with
+// P_4^s, k = 4, k = 5; 2, 3, 4, 5 products).  The paper prints no admissible
+// norms for them; these are the largest ||B||_1 at which the Sec. 3 error
+// series (150 terms) of the cosine part, and of the sine part divided by t,
+// stay <= u (the cosine values are theta_2m^2 of Tables 1-2).
+__host__ __device__ inline double theta_cs(int table, int f) {
+  if (table == 0) return f == 0 ? 3.44587e-3 : f == 1 ? 1.32137e-2 : f == 2 ? 9.62511e-1 : 3.64043;
+  return f == 0 ? 5.22375e-1 : f == 1 ? 7.35401e-1 : f == 2 ? 8.96121 : 21.8484;
+}
+__host__ __device__ inline int cs_family_products(int f) { return f + 2; }
+
+// Minimal Pi + 2 sigma with ||B||_1 / 4^sigma <= theta_cs; 0, 3 or 4 as select_family.
+__host__ __device__ inline int select_cs_family(double normB, int table, int* f_out, int* s_out) {
+  if (!isfinite(normB)) return 3;
+  int best = -1, best_s = 0, best_cost = 1 << 30;
+  for (int f = 0; f < 4; ++f) {
+    int sg = 0;
+    while (sg <= kSelMaxS && ldexp(normB, -2 * sg) > theta_cs(table, f)) ++sg;
+    if (sg > kSelMaxS) continue;
+    const int cost = cs_family_products(f) + 2 * sg;
+    if (cost < best_cost || (cost == best_cost && sg < best_s)) {
+      best = f;
+      best_s = sg;
+      best_cost = cost;
+    }
+  }
+  if (best < 0) return 4;
+  *f_out = best;
+  *s_out = best_s;
+  return 0;
+}
+
 }  // namespace cs
