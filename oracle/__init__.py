@@ -130,7 +130,8 @@ def cossin(A, prec: str = "double", m: int | None = None, s: int | None = None):
     """Return (cos(A), sin(A), info) in FP64.
 
     ``m``/``s`` force the family 2m and the number of double-angle steps;
-    both or neither must be given.
+    both or neither must be given.  ``m = 9`` is the 2m = 8 cosine with the
+    five-product T9 sine of eq. Algorithm5sA.
     """
     A = _f64(A)
     n = A.shape[0]

@@ -210,6 +210,43 @@ done:
   return rc;
 }
 
+/* The k = 4 alternative with a five-product sine: T8c of eq. Algorithm4cA and
+ * T9s of eq. Algorithm5sA, whose A8' = A4 (-A2/7! + A4/9!) costs one more
+ * product than the (6!/7!) A8 reuse of T_{7,9}s but matches sin through A^9.
+ * Not used in Tables 1-2; reached only by forcing 2m = 9. */
+static int chain_m9(const double* As, const double* A2, long n, double* C, double* S) {
+  int rc = ORC_OK;
+  double *A4 = NULL, *R = NULL, *A8 = NULL, *Q = NULL;
+  NEWMAT(A4); NEWMAT(R); NEWMAT(A8); NEWMAT(Q);
+  matmul(A2, A2, A4, n);                                   /* A4 = A2^2 */
+  {
+    const double c[2] = {-1.0 / 720.0, 1.0 / 40320.0};     /* -1/6!, 1/8! */
+    const double* M[2] = {A2, A4};
+    lincomb(R, n, 0.0, 2, c, M);
+  }
+  matmul(A4, R, A8, n);                                    /* A8 = A4 (...) */
+  {
+    const double c[3] = {-1.0 / 2.0, 1.0 / 24.0, 1.0};
+    const double* M[3] = {A2, A4, A8};
+    lincomb(C, n, 1.0, 3, c, M);                           /* T8c */
+  }
+  {
+    const double c[2] = {-1.0 / 5040.0, 1.0 / 362880.0};   /* -1/7!, 1/9! */
+    const double* M[2] = {A2, A4};
+    lincomb(R, n, 0.0, 2, c, M);
+  }
+  matmul(A4, R, Q, n);                                     /* A8' = A4 (...) */
+  {
+    const double c[3] = {-1.0 / 6.0, 1.0 / 120.0, 1.0};
+    const double* M[3] = {A2, A4, Q};
+    lincomb(R, n, 1.0, 3, c, M);
+  }
+  matmul(As, R, S, n);                                     /* T9s = A (...) */
+done:
+  free(A4); free(R); free(A8); free(Q);
+  return rc;
+}
+
 /* k = 6 products: eq. Algorithm6cA with coefficients eq:cosm8 (T16c) and
  * eq. Algorithm6sA with the z list printed after it (T_{17,25}s). */
 static int chain_m16(const double* As, const double* A2, long n, double* C, double* S) {
@@ -350,14 +387,15 @@ done:
 /*
  * cos(A) and sin(A) of a dense row-major n x n FP64 matrix.
  *   prec      0 = double table (u = 2^-53), 1 = single table (u = 2^-24)
- *   force_m   -1 for the automatic choice, else 4, 8, 16 or 24
+ *   force_m   -1 for the automatic choice, else 4, 8, 16 or 24, or 9 for
+ *             T8c with the five-product sine T9s (eq. Algorithm5sA)
  *   force_s   -1 for the automatic choice, else 0 .. 64
  * C, S: caller-owned n x n outputs.  info may be NULL.
  */
 int oracle_cossin(const double* A, long n, int prec, int force_m, int force_s,
                   double* C, double* S, oracle_info* info) {
   if (n < 0 || prec < 0 || prec > 1) return ORC_EINVAL;
-  if (force_m != -1 && force_m != 4 && force_m != 8 && force_m != 16 && force_m != 24)
+  if (force_m != -1 && force_m != 4 && force_m != 8 && force_m != 9 && force_m != 16 && force_m != 24)
     return ORC_EINVAL;
   if (force_s < -1 || force_s > ORC_MAX_S) return ORC_EINVAL;
   if ((force_m == -1) != (force_s == -1)) return ORC_EINVAL;
@@ -371,12 +409,12 @@ int oracle_cossin(const double* A, long n, int prec, int force_m, int force_s,
     m = force_m;
     s = force_s;
   }
-  int f = (m == 4) ? 0 : (m == 8) ? 1 : (m == 16) ? 2 : 3;
+  int f = (m == 4) ? 0 : (m == 8 || m == 9) ? 1 : (m == 16) ? 2 : 3;
   if (info) {
     info->norm1 = nrm;
     info->m = m;
     info->s = s;
-    info->products = PI_2M[f] + 2 * s;
+    info->products = PI_2M[f] + (m == 9) + 2 * s;  /* T9s: one product more */
   }
   if (n == 0) return ORC_OK;
 
@@ -387,6 +425,7 @@ int oracle_cossin(const double* A, long n, int prec, int force_m, int force_s,
   switch (m) {
     case 4: rc = chain_m4(As, A2, n, C, S); break;
     case 8: rc = chain_m8(As, A2, n, C, S); break;
+    case 9: rc = chain_m9(As, A2, n, C, S); break;
     case 16: rc = chain_m16(As, A2, n, C, S); break;
     default: rc = chain_m24(As, A2, n, C, S); break;
   }

@@ -19,7 +19,7 @@ import oracle
 import paper_poly as pp
 from paper_2010_00465_gb300 import inputs
 
-FAM = {4: ("c4", "s5", 4, 5), 8: ("c8", "s79", 8, 7), 16: ("c16", "s17", 16, 17),
+FAM = {4: ("c4", "s5", 4, 5), 8: ("c8", "s79", 8, 7), 9: ("c8", "s9", 8, 9), 16: ("c16", "s17", 16, 17),
        24: ("c24", "s23", 24, 21)}
 U = {"double": 2.0 ** -53, "single": 2.0 ** -24}
 
@@ -53,6 +53,8 @@ def test_theta_recomputed_from_error_series():
     polys = pp.schemes(refined=True)
     for prec in ("double", "single"):
         for m, (ck, sk, _, _) in FAM.items():
+            if m == 9:
+                continue  # no table entry; see test_t9_sine_variant
             for key, sine in ((ck, False), (sk, True)):
                 th = float(pp.theta(polys[key], sine, mp.mpf(2) ** (-53 if prec == "double" else -24)))
                 got = oracle.theta(prec, m, sine)
@@ -131,7 +133,7 @@ def test_norm1_definition():
 
 # ------------------------------------------------- scheme coefficients ---
 
-@pytest.mark.parametrize("m", [4, 8, 16, 24])
+@pytest.mark.parametrize("m", [4, 8, 9, 16, 24])
 def test_chain_coefficients_on_nilpotent_shift(m):
     """For the shift matrix N (N^k has ones on the k-th superdiagonal and
     N^d = 0), p(N) has the coefficient of A^k of the approximant p in entry
@@ -156,7 +158,7 @@ def test_chain_coefficients_on_nilpotent_shift(m):
     assert np.allclose(np.triu(C, 0)[1, 1:], C[0, :-1], rtol=1e-14, atol=0)
 
 
-@pytest.mark.parametrize("m,s", [(24, 3), (16, 2), (8, 1), (4, 2)])
+@pytest.mark.parametrize("m,s", [(24, 3), (16, 2), (8, 1), (9, 2), (4, 2)])
 def test_double_angle_on_nilpotent_shift(m, s):
     """With s double-angle steps on A_s = 2^-s A, the composite approximant
     still matches the Taylor series of cos A and sin A through the family's
@@ -339,6 +341,32 @@ def test_truncation_bound_at_theta(m, prec):
         es = abs(S[0, 0] - float(mp.sin(x)))
         assert ec <= U[prec] + 4 * 2.0 ** -53, (m, x, ec)
         assert es <= U[prec] + 4 * 2.0 ** -53 * max(1, x), (m, x, es)
+
+
+@pytest.mark.parametrize("prec", ["double", "single"])
+def test_t9_sine_variant(prec):
+    """2m = 9: T8c with the five-product sine T9s (eq. Algorithm5sA).  Its
+    sine's admissible norm, recomputed from the Sec. 3 series (the paper
+    prints none), is 0.17402 (double) / 1.0813 (single), above the cosine's
+    Table value, so the pair is bound by theta^c_8; at that norm the forward
+    error of both is at most u, and the sine error stays at most u up to its
+    own theta.  It costs 5 products."""
+    polys = pp.schemes()
+    th_s = float(pp.theta(polys["s9"], True, U[prec]))
+    assert th_s == pytest.approx({"double": 0.17402, "single": 1.0813}[prec], rel=2e-4)
+    th = min(oracle.theta(prec, 8, False), th_s)
+    assert th == oracle.theta(prec, 8, False)
+    mp.mp.dps = 40
+    for x in (th, 0.5 * th):
+        C, S, info = oracle.cossin(np.array([[x]]), prec, m=9, s=0)
+        assert info["products"] == 5
+        assert abs(C[0, 0] - float(mp.cos(x))) <= U[prec] + 4 * 2.0 ** -53
+        assert abs(S[0, 0] - float(mp.sin(x))) <= U[prec] + 4 * 2.0 ** -53
+    C, S, _ = oracle.cossin(np.array([[th_s]]), prec, m=9, s=0)
+    assert abs(S[0, 0] - float(mp.sin(th_s))) <= U[prec] + 4 * 2.0 ** -53
+    # the T_{7,9} sine of 2m = 8 is above u there
+    _, S8, _ = oracle.cossin(np.array([[th_s]]), prec, m=8, s=0)
+    assert abs(S8[0, 0] - float(mp.sin(th_s))) > 2 * U[prec]
 
 
 def test_scipy_library_routine():
