@@ -121,7 +121,12 @@ cs_status cossin(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, void* 
  * cossin_workspace_size bytes, 256-byte aligned) so that nothing is
  * allocated, and optional forced (m, s): force_m in {4, 8, 16, 24} together
  * with force_s in [0, 64], or both -1 for the automatic choice (with a forced
- * pair the norm is still computed and reported).  info may be NULL. */
+ * pair the norm is still computed and reported).  force_m = 9 selects the
+ * alternative k = 4 scheme that the automatic choice never takes: the 2m = 8
+ * cosine with the sine T9s of eq. Algorithm5sA (5 products, exact through
+ * A^9; its sine's admissible norm, not printed in the paper, is 0.17402
+ * double / 1.0813 single, so the cosine's Table 1-2 value binds the pair).
+ * info may be NULL. */
 cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, void* S_dev,
                     void* ws_dev, size_t ws_bytes, int32_t force_m, int32_t force_s,
                     cs_info* info, cossin_stream_t stream);
@@ -177,6 +182,36 @@ cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec
 cs_status cossin_backward(int64_t count, int64_t n, const double* A_dev, const double* G_C_dev,
                           const double* G_S_dev, double* dA_dev, double* C_dev, double* S_dev,
                           int32_t force_m, int32_t force_s, cs_info* infos_host, cossin_stream_t stream);
+
+/* ------------------------------------------------------------ unitary ---
+ * The propagator U = e^{-itA} = cos(tA) - i sin(tA) of a real n x n matrix
+ * (Sec. 1, the Schroedinger case: unitary when A is symmetric), by the
+ * cos/sin scheme at tA: ||tA||_1 = |t| ||A||_1 drives the choice of (2m, s)
+ * (Tables 1-2) and t is folded into the first and last products, so no
+ * scaled copy of A is made.
+ *   U_dev: n x n complex, interleaved (re, im) pairs of the precision's real
+ *          type (complex128 for CS_FP64 and CS_SPLIT_TF32, complex64 for
+ *          CS_FP32); must not overlap A.
+ *   ws_dev: at least cossin_unitary_workspace_size bytes, 256-byte aligned,
+ *          or NULL to allocate on `stream`.
+ * force_m / force_s and info as cossin_ex (info->norm1 = ||tA||_1).
+ * CS_EINVAL for a non-finite t. */
+cs_status cossin_unitary_workspace_size(int64_t n, cs_prec prec, size_t* bytes);
+cs_status cossin_unitary(const void* A_dev, int64_t n, double t, cs_prec prec, void* U_dev, void* ws_dev,
+                         size_t ws_bytes, int32_t force_m, int32_t force_s, cs_info* info,
+                         cossin_stream_t stream);
+
+/* Gradient of the real loss L = Re sum conj(G) .* U = <Re G, cos(tA)> +
+ * <-Im G, sin(tA)> with respect to the real A (FP64; `count` matrices of
+ * order n, contiguous), at the (2m, s) the forward pass uses for tA: the
+ * reverse pass of cossin_backward with the cotangents (Re G, -Im G), t
+ * carried by the plans' coefficients.  G_dev: interleaved complex128,
+ * count x n x n.  dA_dev: real.  U_dev: optional interleaved forward output
+ * (NULL to skip).  infos_host as cossin_backward.  No device-side failure
+ * mode beyond those of cossin_backward. */
+cs_status cossin_unitary_backward(int64_t count, int64_t n, double t, const double* A_dev, const double* G_dev,
+                                  double* dA_dev, double* U_dev, int32_t force_m, int32_t force_s,
+                                  cs_info* infos_host, cossin_stream_t stream);
 
 /* ------------------------------------------------------------ batched ---
  * cos and sin of `count` FP32 matrices of orders n[i] <= 256 (host array),

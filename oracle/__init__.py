@@ -181,6 +181,25 @@ def cs_select(normB: float, prec: str = "double"):
     return f.value, s.value
 
 
+def unitary(A, t: float, prec: str = "double", m: int | None = None, s: int | None = None):
+    """U = exp(-i t A) = cos(tA) - i sin(tA) (Sec. 1, the Schroedinger case)
+    from the oracle's cos/sin of tA; returns (U, info)."""
+    A = _f64(A)
+    C, S, info = cossin(float(t) * A, prec, m=m, s=s)
+    return C - 1j * S, info
+
+
+def unitary_gradient(A, t: float, G, m: int, s: int, prec: str = "double") -> np.ndarray:
+    """d/dA of Re sum(conj(G) * U(A)) at fixed (2m, s) of tA.
+
+    Re sum(conj(G) U) = <Re G, cos(tA)> + <-Im G, sin(tA)>, so by the chain
+    rule the gradient is t times the cos/sin gradient at tA with the
+    cotangents (Re G, -Im G)."""
+    A = _f64(A)
+    G = np.asarray(G, dtype=np.complex128)
+    return float(t) * gradient(float(t) * A, G.real.copy(), -G.imag.copy(), m, s, prec)
+
+
 def matmul(X, Y) -> np.ndarray:
     X = _f64(X)
     Y = _f64(Y)

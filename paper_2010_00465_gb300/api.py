@@ -193,6 +193,84 @@ def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m:
     return out
 
 
+def unitary_workspace_size(n: int, prec="fp64") -> int:
+    out = ctypes.c_size_t()
+    check(lib().cossin_unitary_workspace_size(int(n), _prec(prec), ctypes.byref(out)))
+    return out.value
+
+
+def unitary(A: torch.Tensor, t: float, prec=None, *, m: int | None = None, s: int | None = None,
+            workspace: torch.Tensor | None = None, stream=None, return_info: bool = False):
+    """U = exp(-i t A) = cos(tA) - i sin(tA) of a real square matrix (complex128
+    for "fp64"/"split_tf32", complex64 for "fp32")."""
+    p = _prec(prec, A)
+    A = A.contiguous()
+    n = _check_matrix(A, p)
+    U = torch.empty((n, n), dtype=torch.complex64 if p == _lib.CS_FP32 else torch.complex128, device=A.device)
+    need = unitary_workspace_size(n, p)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
+    info = CsInfo()
+    fm = -1 if m is None else int(m)
+    fs = -1 if s is None else int(s)
+    check(lib().cossin_unitary(ctypes.c_void_p(A.data_ptr()), n, float(t), p, ctypes.c_void_p(U.data_ptr()),
+                               ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+                               fm, fs, ctypes.byref(info), _stream_ptr(stream)))
+    return (U, info.as_dict()) if return_info else U
+
+
+def unitary_backward(A: torch.Tensor, t: float, G: torch.Tensor, *, m: int | None = None, s: int | None = None,
+                     want_forward: bool = False, stream=None, return_info: bool = False):
+    """d/dA of Re sum(conj(G) * exp(-i t A)) (FP64; A real n x n or [count, n, n],
+    G complex128 of the same shape)."""
+    if A.dtype != torch.float64 or G.dtype != torch.complex128:
+        raise TypeError("the unitary adjoint takes a float64 A and a complex128 G")
+    batched = A.dim() == 3
+    A3 = (A if batched else A.unsqueeze(0)).contiguous()
+    G3 = (G if batched else G.unsqueeze(0)).contiguous()
+    if A3.shape[-1] != A3.shape[-2] or G3.shape != A3.shape:
+        raise ValueError("square A and a G of the same shape expected")
+    if not (A3.is_cuda and G3.is_cuda):
+        raise ValueError("CUDA tensors expected")
+    count, n = A3.shape[0], A3.shape[1]
+    dA = torch.empty_like(A3)
+    U = torch.empty_like(G3) if want_forward else None
+    infos = (CsInfo * max(count, 1))()
+    fm = -1 if m is None else int(m)
+    fs = -1 if s is None else int(s)
+    check(lib().cossin_unitary_backward(count, n, float(t), ctypes.c_void_p(A3.data_ptr()),
+                                        ctypes.c_void_p(G3.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
+                                        ctypes.c_void_p(U.data_ptr() if U is not None else 0), fm, fs, infos,
+                                        _stream_ptr(stream)))
+    if not batched:
+        dA = dA[0]
+        U = U[0] if U is not None else None
+    out = (dA, U) if want_forward else dA
+    if return_info:
+        return out, [infos[i].as_dict() for i in range(count)]
+    return out
+
+
+class Unitary(torch.autograd.Function):
+    """exp(-i t A) for a real FP64 n x n A, with the library's adjoint as backward
+    (gradient with respect to A; t is a constant)."""
+
+    @staticmethod
+    def forward(ctx, A, t):
+        ctx.save_for_backward(A)
+        ctx.t = float(t)
+        return unitary(A, t, "fp64")
+
+    @staticmethod
+    def backward(ctx, gU):
+        (A,) = ctx.saved_tensors
+        return unitary_backward(A, ctx.t, gU.contiguous()), None
+
+
+def unitary_autograd(A: torch.Tensor, t: float):
+    return Unitary.apply(A, t)
+
+
 class CosSin(torch.autograd.Function):
     """(cos A, sin A) with the library's adjoint as backward (FP64; A is n x n
     or a [count, n, n] batch).  The backward recomputes the forward pass with

@@ -103,13 +103,13 @@ struct Ssa {
   std::vector<SsaStep> steps;
 };
 
-Ssa make_ssa(int m, int s) {
+Ssa make_ssa(int m, int s, double scale) {
   Ssa g;
   int cur[SL_COUNT];
   for (int k = 0; k < SL_COUNT; ++k) cur[k] = -1;
   g.A = g.nvalues++;
   cur[SL_A] = g.A;
-  for (const Step& st : chain_plan(m, s)) {
+  for (const Step& st : chain_plan(m, s, scale)) {
     SsaStep q;
     q.X = cur[st.X];
     q.Y = cur[st.Y];
@@ -156,8 +156,8 @@ cs_status gemm_acc(const double* X, bool tX, const double* Y, bool tY, double* A
 }
 
 cs_status run_group(const double* A, const double* GC, const double* GS, double* dA, double* C_out, double* S_out,
-                    int64_t n, int m, int s, int64_t g, cudaStream_t stream) {
-  const Ssa ssa = make_ssa(m, s);
+                    int64_t n, int m, int s, int64_t g, double scale, cudaStream_t stream) {
+  const Ssa ssa = make_ssa(m, s, scale);
   const int64_t n2 = n * n;
   const int nlev = s + 1;
   // values: chain values, then the double-angle levels C_1..C_s, S_1..S_s
@@ -251,15 +251,15 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
 
 int64_t adjoint_products(int m, int s) { return 3 * products_of(m) + 6 * s; }
 
-}  // namespace cs
-
-extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, const double* G_C,
-                                     const double* G_S, double* dA, double* C, double* S, int32_t force_m,
-                                     int32_t force_s, cs_info* infos_host, cossin_stream_t stream) {
-  using namespace cs;
+// Gradient of <G_C, r_c(scale A)> + <G_S, r_s(scale A)> with respect to A; the
+// scale sits in the plans' coefficients, so the reverse pass carries it.
+cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A, const double* G_C,
+                        const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
+                        cs_info* infos_host, cudaStream_t st) {
   if (count < 0 || n < 0 || n > kMaxN) return fail(CS_EINVAL, "count or n out of range");
+  if (!isfinite(scale)) return fail(CS_EINVAL, "t must be finite");
   if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");
-  if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 16 or 24");
+  if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 9, 16 or 24");
   if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_s must be in [0, 64]");
   if (count == 0 || n == 0) return CS_OK;
   if (!A || !G_C || !G_S || !dA) return fail(CS_EINVAL, "null matrix pointer");
@@ -270,7 +270,6 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
   };
   if (ov(dA, A) || ov(dA, G_C) || ov(dA, G_S) || ov(C, A) || ov(S, A) || ov(C, S) || ov(C, dA) || ov(S, dA))
     return fail(CS_EINVAL, "outputs must not overlap inputs or each other");
-  cudaStream_t st = (cudaStream_t)stream;
   // norms of every matrix, one synchronisation
   std::vector<double> norms((size_t)count);
   {
@@ -285,6 +284,7 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpyAsync");
     if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");
   }
+  for (double& v : norms) v *= fabs(scale);
   std::map<std::pair<int, int>, std::vector<int>> groups;
   for (int64_t b = 0; b < count; ++b) {
     int m, s;
@@ -327,7 +327,7 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
       ce = cudaGetLastError();
       if (ce != cudaSuccess) rc = cuda_fail(ce, "gather");
     }
-    if (rc == CS_OK) rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, st);
+    if (rc == CS_OK) rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, scale, st);
     if (rc == CS_OK) {
       scatter_kernel<<<nb, 256, 0, st>>>(gdA, dA, didx, n2, g);
       if (need_c) scatter_kernel<<<nb, 256, 0, st>>>(gC, C, didx, n2, g);
@@ -342,4 +342,13 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
     if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");
   }
   return CS_OK;
+}
+
+}  // namespace cs
+
+extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, const double* G_C,
+                                     const double* G_S, double* dA, double* C, double* S, int32_t force_m,
+                                     int32_t force_s, cs_info* infos_host, cossin_stream_t stream) {
+  return cs::backward_impl(count, n, 1.0, A, G_C, G_S, dA, C, S, force_m, force_s, infos_host,
+                           (cudaStream_t)stream);
 }

@@ -89,6 +89,7 @@ static void prof_drain() {
 
 // -------------------------------------------------------------- selection ---
 int products_of(int m) {
+  if (m == 9) return 5;  // T8c with the five-product sine T9s (eq. Algorithm5sA)
   for (int f = 0; f < 4; ++f)
     if (family_order(f) == m) return family_products(f);
   return -1;
@@ -109,7 +110,7 @@ cs_status select_ms(double norm1, int table, int* m, int* s) {
 // ------------------------------------------------------------- workspace ---
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout make_layout(int64_t n, int prec) {
+Layout make_layout(int64_t n, int prec, bool with_outputs) {
   Layout L;
   const size_t n2 = (size_t)n * (size_t)n;
   size_t off = 0;
@@ -137,6 +138,11 @@ Layout make_layout(int64_t n, int prec) {
       L.ping64[1] = take(sizeof(double) * 2 * n2);
     }
   }
+  if (with_outputs) {
+    const size_t el = prec == CS_FP32 ? sizeof(float) : sizeof(double);
+    L.out_c = take(el * n2);
+    L.out_s = take(el * n2);
+  }
   L.total = off;
   return L;
 }
@@ -146,9 +152,9 @@ Layout make_layout(int64_t n, int prec) {
 // is A itself, SL_C and SL_S receive T^c_2m(A_s) and the sine approximant,
 // W0..W7 hold intermediates.  Every step is P = X Y followed by its epilogue;
 // the first product folds the scaling (A_s)^2 = 4^-s A A and the last folds
-// A_s = 2^-s A into alpha.
-std::vector<Step> chain_plan(int m, int s) {
-  const double a2 = ldexp(1.0, -2 * s), as = ldexp(1.0, -s);
+// A_s = 2^-s A into alpha (times scale^2 and scale for a scaled argument).
+std::vector<Step> chain_plan(int m, int s, double scale) {
+  const double a2 = scale * scale * ldexp(1.0, -2 * s), as = scale * ldexp(1.0, -s);
   std::vector<Step> P;
   auto out = [](int slot, double alpha, double gamma, std::vector<std::pair<int, double>> beta = {},
                 std::vector<std::pair<int, double>> delta = {}) {
@@ -169,6 +175,17 @@ std::vector<Step> chain_plan(int m, int s) {
                                   out(W(4), 1.0 / 120, 1.0, {{W(0), -1.0 / 6}})}});    // I - A2/6 + A4/120
     P.push_back(Step{W(1), W(2), {out(SL_C, 1.0, 0.0, {{W(3), 1.0}}),
                                   out(W(4), 720.0 / 5040.0, 0.0, {{W(4), 1.0}})}});
+    P.push_back(Step{SL_A, W(4), {out(SL_S, as, 0.0)}});
+  } else if (m == 9) {
+    // eq. Algorithm4cA for the cosine and eq. Algorithm5sA for the sine:
+    // A8' = A4(-A2/7! + A4/9!), T9s = A(I - A2/3! + A4/5! + A8') (one product more)
+    P.push_back(Step{W(0), W(0), {out(W(1), 1.0, 0.0),                                   // A4
+                                  out(W(2), 1.0 / 40320, 0.0, {{W(0), -1.0 / 720}}),     // -A2/6! + A4/8!
+                                  out(W(3), 1.0 / 24, 1.0, {{W(0), -0.5}}),              // I - A2/2 + A4/24
+                                  out(W(4), 1.0 / 120, 1.0, {{W(0), -1.0 / 6}}),         // I - A2/6 + A4/120
+                                  out(W(5), 1.0 / 362880, 0.0, {{W(0), -1.0 / 5040}})}}); // -A2/7! + A4/9!
+    P.push_back(Step{W(1), W(2), {out(SL_C, 1.0, 0.0, {{W(3), 1.0}})}});
+    P.push_back(Step{W(1), W(5), {out(W(4), 1.0, 0.0, {{W(4), 1.0}})}});
     P.push_back(Step{SL_A, W(4), {out(SL_S, as, 0.0)}});
   } else if (m == 16) {
     // eq. Algorithm6cA with eq. cosm8, eq. Algorithm6sA with its z list.
@@ -230,9 +247,9 @@ std::vector<Step> chain_plan(int m, int s) {
 }
 
 // ------------------------------------------------------------------ specs ---
-PlanSpec cossin_spec(int m, int s) {
+PlanSpec cossin_spec(int m, int s, double scale) {
   PlanSpec P;
-  P.steps = chain_plan(m, s);
+  P.steps = chain_plan(m, s, scale);
   P.s = s;
   return P;
 }
@@ -356,8 +373,6 @@ cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double*
   return CS_OK;
 }
 
-namespace {
-
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
   const char* pb = (const char*)b;
@@ -371,6 +386,8 @@ cs_status check_prec(cs_prec prec) {
     return fail(CS_EINVAL, "unknown precision");
   return CS_OK;
 }
+
+namespace {
 
 struct PinnedWords {
   double norm;
@@ -405,12 +422,15 @@ cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, cha
                    const PlanSpec& P, cudaStream_t stream);
 cs_status matmul_tf32(const void* X, const void* Y, int64_t n, bool f64_io, void* P, cudaStream_t stream);
 
+// cos and sin of scale * A (scale = 1 for cossin / cossin_ex); the workspace
+// is make_layout(n, prec).total bytes.
 cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
-                      int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream) {
+                      int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream, double scale) {
   CS_CHECK(check_prec(prec));
+  if (!isfinite(scale)) return fail(CS_EINVAL, "t must be finite");
   if (n < 0 || n > kMaxN) return fail(CS_EINVAL, "n out of range [0, 65536]");
   if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");
-  if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 16 or 24");
+  if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 9, 16 or 24");
   if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_s must be in [0, 64]");
   const int table = prec == CS_FP64 ? 0 : 1;
   if (n == 0) {
@@ -433,6 +453,8 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   double nrm = 0.0;
   CS_CHECK(read_norm(nrm_dev, &nrm, stream));
   if (!isfinite(nrm)) return fail(CS_ENONFINITE, "||A||_1 is not finite");
+  nrm *= fabs(scale);
+  if (!isfinite(nrm)) return fail(CS_ENONFINITE, "||t A||_1 is not finite");
   int m, s;
   if (force_m == -1) {
     CS_CHECK(select_ms(nrm, table, &m, &s));
@@ -442,7 +464,7 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   }
   const int prods = products_of(m) + 2 * s;
   if (info) *info = cs_info{nrm, m, s, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
-  const PlanSpec spec = cossin_spec(m, s);
+  const PlanSpec spec = cossin_spec(m, s, scale);
   if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, stream);
   return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
@@ -540,7 +562,7 @@ cs_status cossin_select(double norm1, int32_t table, int32_t* m, int32_t* s) {
 
 cs_status cossin_ex(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
                     int32_t force_m, int32_t force_s, cs_info* info, cossin_stream_t stream) {
-  return cs::cossin_impl(A, n, prec, C, S, ws, ws_bytes, force_m, force_s, info, (cudaStream_t)stream);
+  return cs::cossin_impl(A, n, prec, C, S, ws, ws_bytes, force_m, force_s, info, (cudaStream_t)stream, 1.0);
 }
 
 cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossin_stream_t stream) {
@@ -555,7 +577,7 @@ cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossi
     cudaGetLastError();
     return cs::fail(CS_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
   }
-  cs_status rc = cs::cossin_impl(A, n, prec, C, S, ws, bytes, -1, -1, nullptr, st);
+  cs_status rc = cs::cossin_impl(A, n, prec, C, S, ws, bytes, -1, -1, nullptr, st, 1.0);
   cudaFreeAsync(ws, st);
   return rc;
 }

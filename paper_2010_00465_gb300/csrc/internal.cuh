@@ -112,6 +112,17 @@ cs_status norm1_batched_f64(const double* A, int64_t n, int64_t count, double* o
 // dst[i] = scale * src[i], i < count (FP64).
 cs_status scale_f64(const double* src, double* dst, int64_t count, double scale, cudaStream_t stream);
 
+// The executors behind the ABI (cossin_api.cu, adjoint.cu): cos/sin and the
+// adjoint of scale * A.
+cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
+                      int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream, double scale);
+cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A, const double* G_C,
+                        const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
+                        cs_info* infos_host, cudaStream_t stream);
+cs_status check_prec(cs_prec prec);
+size_t elem_size(cs_prec p);
+bool overlaps(const void* a, size_t na, const void* b, size_t nb);
+
 // Host selection (step 2).
 cs_status select_ms(double norm1, int table, int* m, int* s);
 int products_of(int m);

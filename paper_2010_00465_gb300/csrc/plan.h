@@ -33,7 +33,9 @@ struct Step {
   std::vector<OutSpec> outs;
 };
 
-std::vector<Step> chain_plan(int m, int s);
+// `scale` evaluates the scheme at scale * A (the unitary e^{-itA} takes t):
+// the first product folds scale^2 4^-s and the last scale 2^-s.
+std::vector<Step> chain_plan(int m, int s, double scale = 1.0);
 
 // What an executor runs: the product steps, then s double-angle steps.  With
 // scale_into_w0 the input is first copied into W0 scaled by input_scale (the
@@ -45,7 +47,7 @@ struct PlanSpec {
   double input_scale = 1.0;
 };
 
-PlanSpec cossin_spec(int m, int s);
+PlanSpec cossin_spec(int m, int s, double scale = 1.0);
 // family 0: k = 3 with P_{3,4}^s, 1: k = 3 with P_4^s, 2: k = 4, 3: k = 5 (Sec. 2.2)
 PlanSpec cs_spec(int family, int sigma, double t);
 int cs_products(int family);
@@ -64,10 +66,11 @@ struct Layout {
   size_t a4[4] = {};
   size_t w4[kWorkSlots][4] = {};
   size_t ping4[2][4] = {};
+  size_t out_c = 0, out_s = 0;  // n x n C and S of the precision's type (with_outputs)
   size_t total = 0;
 };
 
-Layout make_layout(int64_t n, int prec);
+Layout make_layout(int64_t n, int prec, bool with_outputs = false);
 
 // Double-angle steps in FP64 on the stacked buffers ping[2] (each 2n x n):
 // starts from [C; S] in ping[0]; the last step writes C and S.

@@ -38,7 +38,7 @@ def test_matches_oracle_gradient(n, family, nrm):
     assert relfro(dA.cpu().numpy(), ref) <= TOL64
 
 
-@pytest.mark.parametrize("m,s", [(4, 0), (8, 1), (16, 2), (24, 0), (24, 3)])
+@pytest.mark.parametrize("m,s", [(4, 0), (8, 1), (16, 2), (24, 0), (24, 3), (9, 0), (9, 2)])
 def test_every_family_forced(m, s):
     n = 40
     A = inputs.matrix(n, "normal", 0.5 * 2 ** s, index=103, sub=m)

@@ -56,7 +56,7 @@ def test_cossin_fp64_matches_oracle(n, nrm):
     assert relfro(S.cpu(), So) <= TOL64
 
 
-@pytest.mark.parametrize("m", [4, 8, 16, 24])
+@pytest.mark.parametrize("m", [4, 8, 9, 16, 24])
 @pytest.mark.parametrize("s", [0, 1, 3])
 def test_every_family_forced(m, s):
     A = inputs.matrix(96, "normal", 0.5 * 2 ** s, index=42, sub=m)

@@ -70,7 +70,7 @@ def test_matches_oracle(prec, n, nrm):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "split_tf32"])
-@pytest.mark.parametrize("m", [4, 8, 16, 24])
+@pytest.mark.parametrize("m", [4, 8, 9, 16, 24])
 @pytest.mark.parametrize("s", [0, 2])
 def test_every_family_forced(prec, m, s):
     A = inputs.matrix(160, "normal", 2.0 * 2 ** s, index=61, sub=m)
