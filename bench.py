@@ -183,7 +183,7 @@ def main():
     ap.add_argument("--precisions", default=None, help="comma list: fp64,fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the split-precision comparison")
-    ap.add_argument("--ncu-case", default=None, choices=["gemm_tf32", "gemm_f64", "norm1", "batched", "batched256"],
+    ap.add_argument("--ncu-case", default=None, choices=["gemm_tf32", "gemm_f64", "norm1", "batched", "batched256", "gemm_emu"],
                     help="run one small launch set for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -315,17 +315,20 @@ def main():
 
 
 def forms(api, wsp):
-    """Split precision (Taylor chain on tensor cores, FP64 double-angle steps)
-    against the plain FP64 path on the same FP64 input, n = 4096, with the
-    error of each against the FP64 path stated beside it."""
+    """The other precisions at n = 4096 against the plain FP64 path on the same
+    FP64 input: FP64 with every product emulated on the BF16 tensor cores,
+    split precision (Taylor chain on tensor cores) with native or emulated
+    FP64 double-angle products; each with its relative difference to the FP64
+    path stated beside it."""
     import torch
     from paper_2010_00465_gb300 import inputs
     out = {}
+    precs = ("fp64", "fp64_emu", "split_tf32", "split_emu")
     for nrm in (1.0, 16.0, 64.0):
         A = torch.from_numpy(inputs.matrix(N, "normal", nrm, index=2)).cuda()
         row = {}
         res = {}
-        for prec in ("fp64", "split_tf32"):
+        for prec in precs:
             need = api.workspace_size(N, prec)
             ws = wsp if wsp.numel() >= need else torch.empty(need, dtype=torch.uint8, device="cuda")
             api.cossin(A, prec, workspace=ws)
@@ -340,13 +343,44 @@ def forms(api, wsp):
             res[prec] = (C, S)
             row[prec] = {"ms": ms, "m": info["m"], "s": info["s"], "alg_tflops": info["flops"] / ms / 1e9}
         C64, S64 = res["fp64"]
-        Cs, Ss = res["split_tf32"]
-        row["split_rel_err_vs_fp64_path"] = max(float((Cs - C64).norm() / C64.norm()),
-                                                float((Ss - S64).norm() / S64.norm()))
-        row["split_speedup_vs_fp64_path"] = row["fp64"]["ms"] / row["split_tf32"]["ms"]
+        for prec in precs[1:]:
+            Cp, Sp = res[prec]
+            row[prec]["rel_diff_vs_fp64_path"] = max(float((Cp - C64).norm() / C64.norm()),
+                                                     float((Sp - S64).norm() / S64.norm()))
+            row[prec]["speedup_vs_fp64_path"] = row["fp64"]["ms"] / row[prec]["ms"]
         out["norm%g" % nrm] = row
-    return {"n": N, "family": "normal", "split_tf32": out, "batched": batched_form(api),
-            "adjoint": adjoint_form(api), "cs": cs_form(api, wsp)}
+    return {"n": N, "family": "normal", "precisions": out, "fp64_emu_product": emu_product_form(api),
+            "batched": batched_form(api), "adjoint": adjoint_form(api), "cs": cs_form(api, wsp)}
+
+
+def emu_product_form(api, reps=5):
+    """One n = 4096 FP64 product emulated on the BF16 tensor cores: the
+    kernel's time from its own CUDA events, the 36 slice products it issues
+    against the measured BF16 peak, and the FP64 rate it stands for."""
+    import torch
+    from paper_2010_00465_gb300 import inputs
+    X = torch.from_numpy(inputs.matrix(N, "normal", None, index=1)).cuda()
+    Y = torch.from_numpy(inputs.matrix(N, "normal", None, index=5)).cuda()
+    api.matmul(X, Y, "fp64_emu")
+    torch.cuda.synchronize()
+    api.prof_reset()
+    api.prof_enable(True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        api.matmul(X, Y, "fp64_emu")
+    torch.cuda.synchronize()
+    call_ms = (time.perf_counter() - t0) * 1e3 / reps
+    api.prof_enable(False)
+    ms, launches, work = api.prof_read("gemm_emu")
+    kms = ms / max(launches, 1)
+    pk, pk_kind = peaks()
+    issued = 36 * 2.0 * N ** 3 / (kms / 1e3) / 1e12
+    native = 2.0 * N ** 3
+    return {"n": N, "kernel_ms": kms, "call_ms_with_slicing_and_alloc": call_ms,
+            "fp64_equivalent_tflops": native / (kms / 1e3) / 1e12,
+            "roofline": {"bound": "tensor", "achieved": issued, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": issued / pk["bf16_tflops"], "note": "36 BF16 slice products per FP64 product; "
+                         "peak = cuBLAS BF16 burst, " + pk_kind}}
 
 
 def cs_form(api, wsp):
@@ -501,6 +535,10 @@ def ncu_case(name):
     elif name == "gemm_f64":
         X = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
         api.matmul(X, X, "fp64")
+    elif name == "gemm_emu":
+        # one n = 4096 FP64 product emulated on the BF16 tensor cores
+        X = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
+        api.matmul(X, X, "fp64_emu")
     else:
         A = torch.from_numpy(inputs.matrix(2 * N, "normal", 1.0, index=1)).cuda()
         api.norm1(A)

@@ -55,13 +55,26 @@ typedef enum {
   /* FP64 in and out; double table (u = 2^-53); every product in FP64. */
   CS_FP64 = 0,
   /* FP32 in and out; single table (u = 2^-24); every product as a
-   * three-pass TF32 tensor-core product (hi*hi + hi*lo + lo*hi) with FP32
-   * accumulation, linear combinations in FP32. */
+   * four-pass TF32 tensor-core product of (hi, lo) splits with FP32
+   * accumulation (promoted, compensated), linear combinations in FP32. */
   CS_FP32 = 1,
   /* FP64 in and out; single table; the Taylor chain (steps 3-4) as
    * three-pass TF32 tensor-core products, while the norm, the choice of
    * (m, s) and the double-angle steps run in FP64.  Accuracy is FP32-level. */
-  CS_SPLIT_TF32 = 2
+  CS_SPLIT_TF32 = 2,
+  /* FP64 in and out; double table; every product emulated on the BF16
+   * tensor cores: rows of the left and columns of the right operand cut into
+   * eight 7-bit integer slices (57 bits of each row / column maximum), the
+   * 36 slice products with p + q <= 7 summed exactly per level in FP32 and
+   * promoted every 512 k into exact int64 fixed-point sums; the diagonal
+   * entries X[r][r], Y[c][c] are added in FP64 (not part of the paper;
+   * FP64-class accuracy: at most 2^-52 K max|X_i.| max|Y_.j| per entry of a
+   * product in the worst case, below the FP64 product's rounding for N(0,1)
+   * data at n = 4096).  n <= 8192 (CS_EINVAL above). */
+  CS_FP64_EMU = 3,
+  /* As CS_SPLIT_TF32, with the FP64 double-angle products emulated as in
+   * CS_FP64_EMU (n <= 8192). */
+  CS_SPLIT_EMU = 4
 } cs_prec;
 
 /* What one call did. */
@@ -270,7 +283,8 @@ typedef enum {
   CS_KERNEL_BATCHED = 3,    /* flops = sum over matrices of 2 n^3 (Pi_2m + 2 s) */
   CS_KERNEL_ADJOINT = 4,    /* flops = 2 M N K of the reverse-pass products */
   CS_KERNEL_OTHER = 5,      /* splits and conversions; bytes moved */
-  CS_KERNEL_KINDS = 6
+  CS_KERNEL_GEMM_EMU = 6,   /* flops = 2 M N K (the emulated FP64 product, not its 36 slice products) */
+  CS_KERNEL_KINDS = 7
 } cs_kernel_kind;
 
 void cossin_prof_enable(int32_t on);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "ozaki.h"
 #include "plan.h"
 #include "tc_gemm.h"
 #include "theta_table.cuh"
@@ -121,10 +122,14 @@ Layout make_layout(int64_t n, int prec, bool with_outputs) {
   };
   L.norm_partial = take(sizeof(double) * (size_t)norm1_scratch_elems(n));
   L.norm_out = take(sizeof(double));
-  if (prec == CS_FP64) {
+  if (prec == CS_FP64 || prec == CS_FP64_EMU) {
     for (int w = 0; w < kWorkSlots; ++w) L.w[w] = take(sizeof(double) * n2);
     L.ping64[0] = take(sizeof(double) * 2 * n2);
     L.ping64[1] = take(sizeof(double) * 2 * n2);
+    if (prec == CS_FP64_EMU) {
+      L.ozaki_bytes = ozaki_dims(2 * n, n, n).total;  // the stacked double-angle product is the largest
+      L.ozaki = take(L.ozaki_bytes);
+    }
   } else {
     L.ld32 = (n + 31) / 32 * 32;
     const size_t sz = sizeof(float) * (size_t)n * (size_t)L.ld32;
@@ -133,9 +138,13 @@ Layout make_layout(int64_t n, int prec, bool with_outputs) {
       for (int k = 0; k < 4; ++k) L.w4[w][k] = take(sz);
     for (int p = 0; p < 2; ++p)
       for (int k = 0; k < 4; ++k) L.ping4[p][k] = take(k < 2 ? 2 * sz : sz);
-    if (prec == CS_SPLIT_TF32) {
+    if (prec == CS_SPLIT_TF32 || prec == CS_SPLIT_EMU) {
       L.ping64[0] = take(sizeof(double) * 2 * n2);
       L.ping64[1] = take(sizeof(double) * 2 * n2);
+    }
+    if (prec == CS_SPLIT_EMU) {
+      L.ozaki_bytes = ozaki_dims(2 * n, n, n).total;
+      L.ozaki = take(L.ozaki_bytes);
     }
   }
   if (with_outputs) {
@@ -331,7 +340,7 @@ Epilogue<T> build_epilogue(const Step& st, T* const* hi, T* const* lo) {
 }
 
 cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, const Layout& L, const PlanSpec& P,
-                  cudaStream_t stream) {
+                  const F64Product& prod, cudaStream_t stream) {
   double* slot[SL_COUNT] = {};
   double* ping[2] = {(double*)(ws + L.ping64[0]), (double*)(ws + L.ping64[1])};
   const size_t n2 = (size_t)n * (size_t)n;
@@ -343,16 +352,33 @@ cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, co
   if (P.scale_into_w0) CS_CHECK(scale_f64(A, slot[W(0)], (int64_t)n2, P.input_scale, stream));
   for (const Step& st : P.steps) {
     Epilogue<double> e = build_epilogue<double>(st, slot, nullptr);
-    CS_CHECK(gemm_f64(slot[st.X], slot[st.Y], n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, stream));
+    CS_CHECK(prod(slot[st.X], slot[st.Y], n, n, n, e, stream));
   }
-  return square_f64(ping, n, s, C, S, stream);
+  return square_f64(ping, n, s, C, S, stream, prod);
 }
 
 }  // namespace
 
 // Double-angle steps (Sec. 1): [C'; S'] = [C; S] C with C' = 2X - I, S' = 2X,
 // one stacked 2n x n x n product per step, ping-ponging between the buffers.
-cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double* S, cudaStream_t stream) {
+cs_status F64Product::operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
+                                 const Epilogue<double>& e, cudaStream_t stream) const {
+  if (emu_work) return gemm_f64_emu(X, Y, M, N, K, K, N, e, N, emu_work, emu_bytes, err, stream);
+  return gemm_f64(X, Y, M, N, K, K, N, false, false, e, N, 1, 0, 0, 0, stream);
+}
+
+F64Product f64_product(cs_prec prec, char* ws, const Layout& L) {
+  F64Product p;
+  if (prec == CS_FP64_EMU || prec == CS_SPLIT_EMU) {
+    p.emu_work = ws + L.ozaki;
+    p.emu_bytes = L.ozaki_bytes;
+    p.err = tc_error_word();
+  }
+  return p;
+}
+
+cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double* S, cudaStream_t stream,
+                     const F64Product& prod) {
   const size_t n2 = (size_t)n * (size_t)n;
   for (int j = 0; j < s; ++j) {
     double* cur = ping[j & 1];
@@ -368,10 +394,12 @@ cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double*
     e.alpha[1] = 2.0;
     e.gamma[0] = -1.0;
     e.gamma[1] = 0.0;
-    CS_CHECK(gemm_f64(cur, cur, 2 * n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, stream));
+    CS_CHECK(prod(cur, cur, 2 * n, n, n, e, stream));
   }
   return CS_OK;
 }
+
+bool uses_emu(cs_prec p) { return p == CS_FP64_EMU || p == CS_SPLIT_EMU; }
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
@@ -382,7 +410,7 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 size_t elem_size(cs_prec p) { return p == CS_FP32 ? sizeof(float) : sizeof(double); }
 
 cs_status check_prec(cs_prec prec) {
-  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32)
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32 && prec != CS_FP64_EMU && prec != CS_SPLIT_EMU)
     return fail(CS_EINVAL, "unknown precision");
   return CS_OK;
 }
@@ -429,10 +457,11 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   CS_CHECK(check_prec(prec));
   if (!isfinite(scale)) return fail(CS_EINVAL, "t must be finite");
   if (n < 0 || n > kMaxN) return fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (uses_emu(prec) && n > kOzakiMaxK) return fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");
   if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 9, 16 or 24");
   if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_s must be in [0, 64]");
-  const int table = prec == CS_FP64 ? 0 : 1;
+  const int table = (prec == CS_FP64 || prec == CS_FP64_EMU) ? 0 : 1;
   if (n == 0) {
     if (info) *info = cs_info{0.0, force_m == -1 ? 4 : force_m, force_s == -1 ? 0 : force_s, 0, table, 0.0};
     return CS_OK;
@@ -465,7 +494,8 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   const int prods = products_of(m) + 2 * s;
   if (info) *info = cs_info{nrm, m, s, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
   const PlanSpec spec = cossin_spec(m, s, scale);
-  if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, stream);
+  if (prec == CS_FP64 || prec == CS_FP64_EMU)
+    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, f64_product(prec, w, L), stream);
   return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
 
@@ -474,11 +504,12 @@ cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, voi
                   int32_t force_f, int32_t force_s, cs_info* info, cudaStream_t stream) {
   CS_CHECK(check_prec(prec));
   if (n < 0 || n > kMaxN) return fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (uses_emu(prec) && n > kOzakiMaxK) return fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (!isfinite(t)) return fail(CS_EINVAL, "t must be finite");
   if ((force_f == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_family and force_sigma must both be -1 or both set");
   if (force_f < -1 || force_f > 3) return fail(CS_EINVAL, "force_family must be in [0, 3]");
   if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_sigma must be in [0, 64]");
-  const int table = prec == CS_FP64 ? 0 : 1;
+  const int table = (prec == CS_FP64 || prec == CS_FP64_EMU) ? 0 : 1;
   if (n == 0) {
     if (info) *info = cs_info{0.0, force_f == -1 ? 0 : force_f, force_s == -1 ? 0 : force_s, 0, table, 0.0};
     return CS_OK;
@@ -512,7 +543,8 @@ cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, voi
   const int prods = cs_family_products(f) + 2 * sg;
   if (info) *info = cs_info{normB, f, sg, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
   const PlanSpec spec = cs_spec(f, sg, t);
-  if (prec == CS_FP64) return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, stream);
+  if (prec == CS_FP64 || prec == CS_FP64_EMU)
+    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, f64_product(prec, w, L), stream);
   return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
 
@@ -525,6 +557,7 @@ cs_status cossin_workspace_size(int64_t n, cs_prec prec, size_t* bytes) {
   if (!bytes) return cs::fail(CS_EINVAL, "bytes is null");
   CS_CHECK(cs::check_prec(prec));
   if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (cs::uses_emu(prec) && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   *bytes = cs::make_layout(n, prec).total;
   return CS_OK;
 }
@@ -533,6 +566,7 @@ cs_status cossin_norm1(const void* A, int64_t n, cs_prec prec, double* norm1, co
   CS_CHECK(cs::check_prec(prec));
   if (!norm1) return cs::fail(CS_EINVAL, "norm1 is null");
   if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (cs::uses_emu(prec) && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (n == 0) {
     *norm1 = 0.0;
     return CS_OK;
@@ -568,6 +602,7 @@ cs_status cossin_ex(const void* A, int64_t n, cs_prec prec, void* C, void* S, vo
 cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossin_stream_t stream) {
   CS_CHECK(cs::check_prec(prec));
   if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (cs::uses_emu(prec) && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (n == 0) return CS_OK;
   size_t bytes = cs::make_layout(n, prec).total;
   void* ws = nullptr;
@@ -585,20 +620,30 @@ cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossi
 cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, void* P, cossin_stream_t stream) {
   CS_CHECK(cs::check_prec(prec));
   if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (cs::uses_emu(prec) && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (n == 0) return CS_OK;
   if (!X || !Y || !P) return cs::fail(CS_EINVAL, "null matrix pointer");
   const size_t bytes = (size_t)n * (size_t)n * cs::elem_size(prec);
   if (cs::overlaps(P, bytes, X, bytes) || cs::overlaps(P, bytes, Y, bytes))
     return cs::fail(CS_EINVAL, "P must not overlap X or Y");
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == CS_FP64) {
+  if (prec == CS_FP64 || prec == CS_FP64_EMU) {
     cs::Epilogue<double> e;
     e.n_out = 1;
     e.out[0] = (double*)P;
     e.alpha[0] = 1.0;
-    return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
+    if (prec == CS_FP64)
+      return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
+    cs::F64Product prod;
+    prod.emu_bytes = cs::ozaki_dims(n, n, n).total;
+    prod.err = cs::tc_error_word();
+    if (!prod.err) return cs::fail(CS_ECUDA, "cannot resolve the device error word");
+    CS_CUDA_CHECK(cudaMallocAsync(&prod.emu_work, prod.emu_bytes, st));
+    cs_status rc = prod((const double*)X, (const double*)Y, n, n, n, e, st);
+    cudaFreeAsync(prod.emu_work, st);
+    return rc;
   }
-  return cs::matmul_tf32(X, Y, n, prec == CS_SPLIT_TF32, P, st);
+  return cs::matmul_tf32(X, Y, n, prec != CS_FP32, P, st);
 }
 
 cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
@@ -607,6 +652,7 @@ cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, v
   if (ws) return cs::cs_impl(A, n, t, prec, C, S, ws, ws_bytes, force_family, force_sigma, info, st);
   CS_CHECK(cs::check_prec(prec));
   if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
+  if (cs::uses_emu(prec) && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (n == 0) return cs::cs_impl(A, n, t, prec, C, S, nullptr, 0, force_family, force_sigma, info, st);
   const size_t bytes = cs::make_layout(n, prec).total;
   void* buf = nullptr;

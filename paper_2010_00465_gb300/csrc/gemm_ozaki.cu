@@ -1,0 +1,594 @@
+// gemm_ozaki.cu -- FP64 products emulated on the BF16 tensor cores.
+//
+// GB300 runs FP64 at 2 FMA/clk/SM, about 1/1700 of its BF16 tensor rate.  A
+// product of FP64 matrices is carried to the tensor cores with integer slices
+// in the manner of Ozaki's error-free splitting (Ozaki, Ogita, Oishi and Rump,
+// Numer. Algorithms 2012; Mukunoki, Ozaki, Ogita and Imamura, ICCS 2020):
+//
+//   * each row i of X is scaled by 2^-e_i (|x| < 1 after scaling) and cut into
+//     S slices of 7 bits: X_i = 2^(e_i - 7) sum_p a_p 2^(-7p), where a_0 is an
+//     integer in [-128, 128] and a_p (p >= 1) an integer in [-64, 64]; slice p
+//     is stored as the BF16 value a_p 2^(-7p), which is exact (8 significant
+//     bits, power-of-two scale).  Columns of Y likewise with 2^-f_j.
+//   * X Y = 2^(e_i + f_j - 14) sum_{p, q} (A_p B_q).  The pair products with
+//     p + q <= S - 1 are formed on the tensor cores (BF16 in, FP32 out).  With
+//     S = 8 the slices leave a residual of at most 2^-56 max|X_i.| per entry
+//     (and likewise for Y), and the dropped pairs add at most 7 2^-56
+//     max|X_i.| max|Y_.j| per k: in all at most 2^-52 K max|X_i.| max|Y_.j|
+//     per entry in the worst case (random-sign errors grow like sqrt(K)).  With
+//     S = 7 (50 bits) the error of one product of N(0,1) matrices measured
+//     3.4e-15, too coarse for the double-angle steps at ||A||_1 = 64.
+//   * Fixed-point slices lose the small entries of a row whose maximum is a
+//     single large entry, and the method's matrices are often I + E (the
+//     cosine near the identity, I - A_2/2 + ...).  So the entry X[r][r mod K]
+//     of each row and Y[c][c] of each column are left out of the slices and
+//     added exactly in the FP64 epilogue:
+//       X Y = X_off Y_off + X[r][d] Y[d][c] + (c != d ? X[r][c] Y[c][c] : 0),
+//     d = r mod K, so the slices only carry the off-diagonal scales.
+//   * Exactness: all terms of one level L = p + q are integer multiples of
+//     2^(-7L), at most (L + 3) 2^12 of them per k.  With a fresh FP32 TMEM
+//     accumulator per level every 512 k, levels 0..4 are summed exactly (below
+//     2^24 quanta); levels >= 5 share one accumulator.  After every 512 k the
+//     epilogue converts each level to an integer number of 2^-35 quanta
+//     (exactly for levels 0..4; the shared accumulator rounded to one
+//     quantum) and adds it into int64 register sums on the integer pipes, so
+//     the sum over K is exact up to that one rounding per chunk (K <= 8192
+//     keeps it below 2^63).  At the end it converts once to FP64, applies
+//     2^(e_i + f_j - 49) and the method's fused linear combinations, and
+//     writes FP64.
+//
+// The result has FP64-class accuracy (slices carry 57 bits of each row or
+// column maximum; the integer sums round once per 512 k) at a cost of
+// S (S + 1) / 2 = 36 BF16 products.  Exact for operands whose entries need
+// at most 57 bits below their row / column maximum (small integers, say).
+//
+// One CTA computes a 128 x 64 tile (S = 8):
+//   warp 0     TMA producer: all S slices of A (128 x 32) and of B^T (64 x 32)
+//              for one 32-wide k-block per stage, 64-byte swizzle, 2 stages;
+//   warp 1     allocates 512 TMEM columns (6 accumulators of 64 columns) and
+//              issues the MMAs (cta_group::1, M = 128, N = 64, K = 16),
+//              level by level, restarting each accumulator at a chunk start
+//              once the epilogue has read it;
+//   warps 2-9  two per TMEM lane quarter, 32 columns each: after each chunk,
+//              read every accumulator (freeing it at once), add it into the
+//              int64 sums, and at the end run the FP64 epilogue.
+// Every mbarrier wait is bounded; on expiry the CTA stops issuing, waits
+// (bounded) for what it issued, frees TMEM and raises *err.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+#include "ozaki.h"
+#include "sm100_ptx.cuh"
+
+namespace cs {
+namespace {
+
+using namespace ptx;
+
+constexpr int S = kOzakiSlices;        // slices per operand
+constexpr int BM = 128;
+constexpr int BN = 64;
+constexpr int BK = 32;                 // 32 bf16 = 64 bytes = one swizzle row
+constexpr int kChunkKb = 16;           // 16 k-blocks = 512 k per accumulator chunk
+constexpr int kExact = 5;              // levels with their own accumulator
+constexpr int kAcc = kExact + 1;       // plus one for the levels >= kExact
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kCols = BN / 2;          // columns per epilogue warp
+constexpr int kABytes = BM * BK * 2;   // 8 KB per A slice
+constexpr int kBBytes = BN * BK * 2;   // 4 KB per B slice
+constexpr int kStageBytes = S * (kABytes + kBBytes);
+constexpr int kStages = 2;
+constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr uint32_t kTmemCols = 512;
+static_assert(kAcc * BN <= (int)kTmemCols, "accumulators exceed TMEM");
+static_assert(kSmem <= 227 * 1024, "shared memory");
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+// Shared-memory descriptors (built in the MMA loop): K-major, 64-byte
+// swizzle, rows of 64 bytes, 8-row (512-byte) atoms stacked along M/N
+// (stride byte offset 512), version 1, base offset 0 (tiles 1024-aligned).
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__host__ __device__ constexpr int acc_of(int level) { return level < kExact ? level : kExact; }
+
+// ------------------------------------------------------------- slicing ---
+// Exponent e with |x| * 2^-e < 1 for every x of the line: frexp of the max.
+__device__ __forceinline__ int line_exponent(double mx) {
+  int e = 0;
+  if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+  return e;
+}
+
+// S slices of x relative to the line exponent e (|x| < 2^e), by integer
+// arithmetic on the FP64 bit pattern (FP64 arithmetic is slow on GB300):
+// x 2^-e is rounded to the 57-bit fixed-point integer R = x 2^(56 - e)
+// (|R| < 2^56), then cut from the top into balanced base-2^7 digits
+// a_p = round(R_p / 2^(49 - 7p)), R_{p+1} = R_p - a_p 2^(49 - 7p), the last
+// digit taking the exact remainder: |a_0| <= 128, |a_p| <= 64.  Slice p is
+// stored as the BF16 value a_p 2^(-7p) (exact).
+__device__ __forceinline__ void cut(double x, int e, __nv_bfloat16 (&q)[S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long frac = bits & ((1ULL << 52) - 1);
+  const long long mant = (long long)(eb ? (frac | (1ULL << 52)) : frac);  // x = mant 2^(max(eb,1) - 1075)
+  const int sh = (eb ? eb : 1) - 1075 - e + 7 * S;  // R = mant 2^sh
+  long long R;
+  if (sh >= 0)
+    R = mant << sh;  // below 2^(7S) since |x| < 2^e
+  else if (sh > -63)
+    R = (mant + (1LL << (-sh - 1))) >> (-sh);
+  else
+    R = 0;
+  if (bits >> 63) R = -R;
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+    const int pos = 7 * (S - 1 - p);
+    long long a;
+    if (p < S - 1) {
+      a = (R + (1LL << (pos - 1))) >> pos;  // arithmetic shift: round half up
+      R -= a << pos;
+    } else {
+      a = R;
+    }
+    q[p] = __float2bfloat16_rn((float)(int)a * __int_as_float((127 - 7 * p) << 23));  // a 2^(-7p)
+  }
+}
+
+// Row maxima of |X| (rows x cols, leading dimension ld) without the entry
+// X[r][r mod cols], which goes to xd[r]: one warp per row.
+__global__ void __launch_bounds__(256) row_exp_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
+                                                      int64_t ld, int* __restrict__ ex, double* __restrict__ xd) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const int64_t d = row % cols;
+  double mx = 0.0;
+  for (int64_t c = lane; c < cols; c += 32)
+    if (c != d) mx = fmax(mx, fabs(X[row * ld + c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    ex[row] = line_exponent(mx);
+    xd[row] = X[row * ld + d];
+  }
+}
+
+// Column maxima of |Y| as ordered bit patterns (non-negative doubles compare
+// like their bits): atomicMax into colmax[cols], which starts at zero.
+// (Y is square here: the entry Y[c][c] is left out and goes to yd[c].)
+__global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__ Y, int64_t rows, int64_t cols,
+                                                      int64_t ld, unsigned long long* __restrict__ colmax) {
+  const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (c >= cols) return;
+  const int64_t r0 = (int64_t)blockIdx.y * 256;
+  const int64_t r1 = std::min<int64_t>(rows, r0 + 256);
+  double mx = 0.0;
+  for (int64_t r = r0; r < r1; ++r)
+    if (r != c) mx = fmax(mx, fabs(Y[r * ld + c]));
+  atomicMax(colmax + c, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void col_exp_kernel(const double* __restrict__ Y, int64_t ld, const unsigned long long* __restrict__ colmax,
+                               int64_t cols, int* __restrict__ ex, double* __restrict__ yd) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cols) {
+    ex[c] = line_exponent(__longlong_as_double((long long)colmax[c]));
+    yd[c] = Y[c * ld + c];
+  }
+}
+
+// Left operand: out[s][r][k] (row-major, K contiguous) for r < rows_pad,
+// k < ldk; rows >= rows and k >= cols are zero.
+__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
+                                                         int64_t ld, const int* __restrict__ ex,
+                                                         __nv_bfloat16* __restrict__ out, int64_t rows_pad,
+                                                         int64_t ldk) {
+  const int64_t total = rows_pad * ldk;
+  const int64_t plane = rows_pad * ldk;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ldk, k = i - r * ldk;
+    __nv_bfloat16 q[S];
+    const double x = (r < rows && k < cols && k != r % cols) ? X[r * ld + k] : 0.0;
+    cut(x, r < rows ? ex[r] : 0, q);
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[s * plane + i] = q[s];
+  }
+}
+
+// Right operand Y (rows = K, cols = N, row-major): out[s][c][k], the
+// transposed slices (K contiguous) for c < cols_pad, k < ldk, through a
+// 32 x 32 shared-memory tile per slice.
+__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int64_t cols,
+                                                         int64_t ld, const int* __restrict__ ex,
+                                                         __nv_bfloat16* __restrict__ out, int64_t cols_pad,
+                                                         int64_t ldk) {
+  __shared__ __nv_bfloat16 tile[S][32][34];
+  const int64_t k0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t k = k0 + j, c = c0 + tx;
+    const double y = (k < rows && c < cols && k != c) ? Y[k * ld + c] : 0.0;
+    __nv_bfloat16 q[S];
+    cut(y, c < cols ? ex[c] : 0, q);
+#pragma unroll
+    for (int s = 0; s < S; ++s) tile[s][j][tx] = q[s];
+  }
+  __syncthreads();
+  const int64_t plane = cols_pad * ldk;
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t c = c0 + j, k = k0 + tx;
+    if (c >= cols_pad || k >= ldk) continue;
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[s * plane + c * ldk + k] = tile[s][tx][j];
+  }
+}
+
+// ---------------------------------------------------------------- product ---
+__device__ __forceinline__ double pow2(int e) {
+  if (e > -1023 && e < 1024) return __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(1.0, e);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ozaki_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int M, int N, int K,
+                 int Mpad, int Npad, const int* __restrict__ ex, const int* __restrict__ fx,
+                 const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y, int64_t ldy,
+                 const double* __restrict__ xd, const double* __restrict__ yd, int64_t ldo,
+                 const __grid_constant__ Epilogue<double> epi, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t chunk_bar;
+  __shared__ __align__(8) uint64_t free_bar[kAcc];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int kb_consumed;
+  __shared__ int chunks_committed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int num_kb = (K + BK - 1) / BK;
+  const int num_chunks = (num_kb + kChunkKb - 1) / kChunkKb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&chunk_bar, 1);
+    for (int a = 0; a < kAcc; ++a) mbar_init(&free_bar[a], kEpiWarps);
+    abort_flag = 0;
+    kb_consumed = 0;
+    chunks_committed = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  int kb_issued = 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch(&mA);
+      tma_prefetch(&mB);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int st = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty_bar[st], ((kb / kStages) & 1) ^ 1, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        uint8_t* base = smem + st * kStageBytes;
+        mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+        for (int s = 0; s < S; ++s) {
+          tma_load_2d(base + s * kABytes, &mA, &full_bar[st], kb * BK, s * Mpad + m0);
+          tma_load_2d(base + S * kABytes + s * kBBytes, &mB, &full_bar[st], kb * BK, s * Npad + n0);
+        }
+        kb_issued = kb + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // Descriptor words: the low word carries the start address (>> 4) and
+      // LBO = 1, the high word SBO = 512 B, version 1 and the 64-byte
+      // swizzle; every operand of a stage is at a compile-time offset from
+      // the stage base, so each MMA costs two integer adds to issue.
+      constexpr uint32_t kDescHi = (512u >> 4) | (1u << 14) | (4u << 29);
+      int kb = 0;
+      for (int c = 0; c < num_chunks && !abort_flag; ++c) {
+        for (int kk = 0; kk < kChunkKb && kb < num_kb; ++kk, ++kb) {
+          const int st = kb % kStages;
+          if (!mbar_wait(&full_bar[st], (kb / kStages) & 1, &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_lo = ((smem_u32(smem + st * kStageBytes) & 0x3FFFFu) >> 4) | (1u << 16);
+          const uint32_t b_lo = a_lo + (uint32_t)((S * kABytes) >> 4);
+          const uint32_t restart_acc = kk == 0 ? 0u : 1u;  // fresh accumulators at a chunk start
+          const bool wait_free = kk == 0 && c > 0;
+          bool stop = false;
+#pragma unroll
+          for (int L = 0; L < S; ++L) {
+            // before an accumulator's first MMA of a chunk, wait until the
+            // epilogue has read it (previous chunk)
+            if (L <= kExact && wait_free) {
+              if (!mbar_wait(&free_bar[acc_of(L)], (c - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                stop = true;
+                break;
+              }
+              tc_fence_after();
+            }
+            const uint32_t d = tmem + (uint32_t)(acc_of(L) * BN);
+#pragma unroll
+            for (int p = 0; p <= L; ++p) {
+              const int q = L - p;
+#pragma unroll
+              for (int j = 0; j < BK / 16; ++j) {  // K = 16 bf16 (32 bytes) per instruction
+                const uint64_t ad =
+                    ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
+                const uint64_t bd =
+                    ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
+                mma_bf16(d, ad, bd, kIdesc, (L <= kExact && p == 0 && j == 0) ? restart_acc : 1u);
+              }
+            }
+          }
+          if (stop) break;
+          mma_commit(&empty_bar[st]);
+          kb_consumed = kb + 1;
+        }
+        mma_commit(&chunk_bar);  // also tracks the MMAs of an aborted chunk
+        chunks_committed = c + 1;
+      }
+    }
+  } else {
+    const int quarter = warp & 3;                // TMEM lanes 32*quarter .. +31
+    const int col0 = ((warp - 2) >> 2) * kCols;  // this warp's 32 columns
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    // Fixed-point sums with quantum 2^-35 of the slice products: each
+    // chunk's level-L value (L <= 4) is an integer multiple of 2^(-7L) below
+    // 2^24 quanta and converts exactly; the levels above 4 are rounded to
+    // 2^-35.  For K <= 8192 the sum stays below 2^63.
+    long long acc[kCols];
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) acc[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < num_chunks; ++c) {
+      int w = 1;
+      if (lane == 0) {
+        w = mbar_wait(&chunk_bar, c & 1, &abort_flag) && !abort_flag;
+        if (!w) abort_flag = 1;
+      }
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (!w) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll 1
+      for (int a = 0; a < kAcc; ++a) {
+        uint32_t v0[16], v1[16];
+        const uint32_t t = tmem + lane_off + (uint32_t)(a * BN + col0);
+        tmem_ld16(t, v0);
+        tmem_ld16(t + 16u, v1);
+        tmem_ld_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&free_bar[a]);
+        const int e = a < kExact ? 7 * a : 35;                 // value * 2^e is an integer (or rounded to one)
+        const float sc = __int_as_float((127 + e) << 23);
+        const long long unit = 1LL << (35 - e);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          acc[j] += (long long)__float2int_rn(__uint_as_float(v0[j]) * sc) * unit;
+          acc[16 + j] += (long long)__float2int_rn(__uint_as_float(v1[j]) * sc) * unit;
+        }
+      }
+    }
+    const int r = m0 + quarter * 32 + lane;
+    if (ok && r < M) {
+      const int er = ex[r] - 14 - 35;
+      const int d = r % K;
+      const double xdr = xd[r];
+      const double* __restrict__ yrow = Y + (int64_t)d * ldy;
+      const double* __restrict__ xrow = X + (int64_t)r * ldx;
+      // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
+      auto full = [&](int j, int cc) {
+        const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
+        return fma((double)acc[j], pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
+      };
+      if (epi.split_row >= 0) {
+        const bool top = r < epi.split_row;
+        const int64_t rr = top ? r : r - epi.split_row;
+        const int t = top ? 0 : 1;
+#pragma unroll
+        for (int j = 0; j < kCols; ++j) {
+          const int cc = n0 + col0 + j;
+          if (cc >= N) break;
+          const double p = full(j, cc);
+          epi.out[t][rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kCols; ++j) {
+          const int cc = n0 + col0 + j;
+          if (cc >= N) break;
+          const double p = full(j, cc);
+          const int64_t idx = (int64_t)r * ldo + cc;
+          double in[EPI_MAX_IN], o[EPI_MAX_OUT];
+#pragma unroll
+          for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
+#pragma unroll
+          for (int t = 0; t < EPI_MAX_OUT; ++t) {
+            if (t >= epi.n_out) break;
+            double v = epi.alpha[t] * p + (r == cc ? epi.gamma[t] : 0.0);
+#pragma unroll
+            for (int q = 0; q < EPI_MAX_IN; ++q)
+              if (q < epi.n_in) v += epi.beta[t][q] * in[q];
+#pragma unroll
+            for (int u = 0; u < EPI_MAX_OUT; ++u)
+              if (u < t) v += epi.delta[t][u] * o[u];
+            o[t] = v;
+          }
+#pragma unroll
+          for (int t = 0; t < EPI_MAX_OUT; ++t) {
+            if (t >= epi.n_out) break;
+            epi.out[t][idx] = o[t];
+          }
+        }
+      }
+    }
+  }
+
+  // Teardown: if a wait expired, wait (bounded) for the copies and MMAs this
+  // CTA issued before freeing TMEM.
+  __syncthreads();
+  if (abort_flag) {
+    if (warp == 0 && lane == 0) {
+      volatile int never = 0;
+      for (int kb = kb_consumed; kb < kb_issued; ++kb)
+        mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1, &never);
+    }
+    if (warp == 1 && lane == 0 && chunks_committed > 0) {
+      volatile int never = 0;
+      const int c = chunks_committed - 1;
+      mbar_wait(&chunk_bar, c & 1, &never);
+    }
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------ tensor maps ---
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Row-major BF16 matrix [rows][cols] (leading dimension ld elements), box of
+// 32 columns x box_rows rows, 64-byte swizzle.
+cs_status make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(CS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (((uintptr_t)base & 15) || (ld * 2) % 16) return fail(CS_EINVAL, "TMA operand not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(CS_ECUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+  return CS_OK;
+}
+
+int grid_for(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256, 152 * 16); }
+
+}  // namespace
+
+OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K) {
+  OzakiDims d;
+  d.Mpad = (M + BM - 1) / BM * BM;
+  d.Npad = (N + BN - 1) / BN * BN;
+  d.ldk = (K + BK - 1) / BK * BK;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  d.a_bytes = al((size_t)S * d.Mpad * d.ldk * 2);
+  d.b_bytes = al((size_t)S * d.Npad * d.ldk * 2);
+  d.ex_bytes = al(sizeof(int) * (size_t)d.Mpad);
+  d.fx_bytes = al(sizeof(int) * (size_t)d.Npad);
+  d.colmax_bytes = al(sizeof(unsigned long long) * (size_t)d.Npad);
+  d.xd_bytes = al(sizeof(double) * (size_t)d.Mpad);
+  d.yd_bytes = al(sizeof(double) * (size_t)d.Npad);
+  d.total = d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes + d.colmax_bytes + d.xd_bytes + d.yd_bytes;
+  return d;
+}
+
+cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
+                       const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
+                       cudaStream_t stream) {
+  if (M <= 0 || N <= 0) return CS_OK;
+  if (M > (1 << 20) || N > (1 << 20) || K > (1 << 20)) return fail(CS_EINVAL, "gemm_f64_emu: size too large");
+  if (K <= 0 || N != K) return fail(CS_EINVAL, "gemm_f64_emu: the right operand must be square");
+  if (K > kOzakiMaxK) return fail(CS_EINVAL, "gemm_f64_emu: K above 8192 (the int64 sums would overflow)");
+  const OzakiDims d = ozaki_dims(M, N, K);
+  if (!work || work_bytes < d.total || ((uintptr_t)work & 255)) return fail(CS_EINVAL, "gemm_f64_emu: workspace");
+  if (!err) return fail(CS_ECUDA, "gemm_f64_emu: no device error word");
+  if ((int64_t)S * d.Mpad > INT32_MAX || (int64_t)S * d.Npad > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: too large");
+  char* w = (char*)work;
+  __nv_bfloat16* a_sl = (__nv_bfloat16*)w;
+  __nv_bfloat16* b_sl = (__nv_bfloat16*)(w + d.a_bytes);
+  int* ex = (int*)(w + d.a_bytes + d.b_bytes);
+  int* fx = (int*)(w + d.a_bytes + d.b_bytes + d.ex_bytes);
+  unsigned long long* colmax = (unsigned long long*)(w + d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes);
+  double* xd = (double*)((char*)colmax + d.colmax_bytes);
+  double* yd = (double*)((char*)xd + d.xd_bytes);
+  {
+    ProfScope prof(CS_KERNEL_OTHER, (double)(M * K + K * N) * (8.0 + 2.0 * S), stream);
+    row_exp_kernel<<<(unsigned)((M + 7) / 8), 256, 0, stream>>>(X, M, K, ldx, ex, xd);
+    CS_CUDA_CHECK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)N, stream));
+    col_max_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)((K + 255) / 256)), 256, 0, stream>>>(Y, K, N, ldy,
+                                                                                                      colmax);
+    col_exp_kernel<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(Y, ldy, colmax, N, fx, yd);
+    slice_rows_kernel<<<grid_for(d.Mpad * d.ldk), 256, 0, stream>>>(X, M, K, ldx, ex, a_sl, d.Mpad, d.ldk);
+    slice_cols_kernel<<<dim3((unsigned)(d.Npad / 32), (unsigned)(d.ldk / 32)), 256, 0, stream>>>(Y, K, N, ldy, fx,
+                                                                                                 b_sl, d.Npad, d.ldk);
+    CS_CUDA_CHECK(cudaGetLastError());
+  }
+  ProfScope prof(CS_KERNEL_GEMM_EMU, 2.0 * (double)M * (double)N * (double)K, stream);
+  CUtensorMap mA, mB;
+  CS_CHECK(make_map(&mA, a_sl, (int64_t)S * d.Mpad, d.ldk, d.ldk, BM));
+  CS_CHECK(make_map(&mB, b_sl, (int64_t)S * d.Npad, d.ldk, d.ldk, BN));
+  static bool attr_set = false;
+  if (!attr_set) {
+    CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)(d.Npad / BN), (unsigned)(d.Mpad / BM));
+  if (grid.y > 65535) return fail(CS_EINVAL, "gemm_f64_emu: grid too large");
+  ozaki_kernel<<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex, fx,
+                                                  X, ldx, Y, ldy, xd, yd, ldo, epi, err);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
+}  // namespace cs

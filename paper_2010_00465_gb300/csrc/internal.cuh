@@ -120,6 +120,7 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
                         cs_info* infos_host, cudaStream_t stream);
 cs_status check_prec(cs_prec prec);
+bool uses_emu(cs_prec p);  // CS_FP64_EMU, CS_SPLIT_EMU: FP64 products emulated on the tensor cores
 size_t elem_size(cs_prec p);
 bool overlaps(const void* a, size_t na, const void* b, size_t nb);
 

@@ -193,7 +193,7 @@ cs_status static_scratch(double** out) {
 
 extern "C" cs_status cossin_norm1_noalloc(const void* A, int64_t n, cs_prec prec, double* norm1_dev,
                                           cossin_stream_t stream) {
-  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32) return cs::fail(CS_EINVAL, "unknown precision");
+  if (cs::check_prec(prec) != CS_OK) return CS_EINVAL;
   if (n < 0) return cs::fail(CS_EINVAL, "n must be >= 0");
   if (n > cs::kStaticMaxN)
     return cs::fail(CS_EINVAL, "cossin_norm1_noalloc: n = " + std::to_string(n) +

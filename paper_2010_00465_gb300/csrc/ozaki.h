@@ -1,0 +1,37 @@
+// ozaki.h -- FP64 products emulated on the BF16 tensor cores (gemm_ozaki.cu).
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cs {
+
+#ifndef COSSIN_OZAKI_SLICES
+#define COSSIN_OZAKI_SLICES 8
+#endif
+// 7-bit slices per operand: 57 bits of each row / column maximum (8 slices)
+constexpr int kOzakiSlices = COSSIN_OZAKI_SLICES;
+
+constexpr int64_t kOzakiMaxK = 8192;  // inner dimension limit of the int64 sums
+
+// Scratch of one emulated product: the BF16 slices of both operands, their
+// row / column exponents and the column maxima.
+struct OzakiDims {
+  int64_t Mpad = 0, Npad = 0, ldk = 0;
+  size_t a_bytes = 0, b_bytes = 0, ex_bytes = 0, fx_bytes = 0, colmax_bytes = 0, xd_bytes = 0, yd_bytes = 0;
+  size_t total = 0;
+};
+OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K);
+
+// P = X Y (X: M x K, Y: K x K, row-major FP64; M = K or the stacked 2K) with
+// the fused FP64 epilogue of gemm_f64 (stacked mode included); the entries
+// X[r][r mod K] and Y[c][c] are added exactly in FP64, the rest is emulated.
+// `work` holds ozaki_dims(M, N, K).total bytes (256-byte aligned).  A
+// bounded wait that expires raises *err.
+cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
+                       const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
+                       cudaStream_t stream);
+
+}  // namespace cs

@@ -66,14 +66,28 @@ struct Layout {
   size_t a4[4] = {};
   size_t w4[kWorkSlots][4] = {};
   size_t ping4[2][4] = {};
+  size_t ozaki = 0, ozaki_bytes = 0;  // scratch of one emulated product (CS_FP64_EMU)
   size_t out_c = 0, out_s = 0;  // n x n C and S of the precision's type (with_outputs)
   size_t total = 0;
 };
 
 Layout make_layout(int64_t n, int prec, bool with_outputs = false);
 
+// How the FP64 executors form a product P = X Y (row-major, X: M x K, Y: K x N)
+// with its epilogue: natively (gemm_f64) or, with emu_work set, emulated on
+// the tensor cores (gemm_f64_emu) using that scratch.
+struct F64Product {
+  void* emu_work = nullptr;
+  size_t emu_bytes = 0;
+  int* err = nullptr;
+  cs_status operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
+                       const Epilogue<double>& e, cudaStream_t stream) const;
+};
+F64Product f64_product(cs_prec prec, char* ws, const Layout& L);
+
 // Double-angle steps in FP64 on the stacked buffers ping[2] (each 2n x n):
 // starts from [C; S] in ping[0]; the last step writes C and S.
-cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double* S, cudaStream_t stream);
+cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double* S, cudaStream_t stream,
+                     const F64Product& prod = F64Product{});
 
 }  // namespace cs

@@ -132,7 +132,7 @@ cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, cha
   double* p64[2] = {(double*)(ws + L.ping64[0]), (double*)(ws + L.ping64[1])};
   CS_CHECK(combine_f64(ping[0].hi, ping[0].lo, n, ld, p64[0], stream));
   CS_CHECK(combine_f64(ping[0].hi + n * ld, ping[0].lo + n * ld, n, ld, p64[0] + n * n, stream));
-  return square_f64(p64, n, s, (double*)C, (double*)S, stream);
+  return square_f64(p64, n, s, (double*)C, (double*)S, stream, f64_product(prec, ws, L));
 }
 
 // One plain product on the tensor-core kernel (used by cossin_matmul).
