@@ -379,7 +379,8 @@ def emu_product_form(api, reps=5):
     return {"n": N, "kernel_ms": kms, "call_ms_with_slicing_and_alloc": call_ms,
             "fp64_equivalent_tflops": native / (kms / 1e3) / 1e12,
             "roofline": {"bound": "tensor", "achieved": issued, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                         "frac": issued / pk["bf16_tflops"], "note": "36 BF16 slice products per FP64 product; "
+                         "frac": issued / pk["bf16_tflops"], "traffic": traffic_of("ozaki_kernel"),
+                         "note": "36 BF16 slice products per FP64 product; "
                          "peak = cuBLAS BF16 burst, " + pk_kind}}
 
 
