@@ -26,16 +26,15 @@
 //       X Y = X_off Y_off + X[r][d] Y[d][c] + (c != d ? X[r][c] Y[c][c] : 0),
 //     d = r mod K, so the slices only carry the off-diagonal scales.
 //   * Exactness: all terms of one level L = p + q are integer multiples of
-//     2^(-7L), at most (L + 3) 2^12 of them per k.  With a fresh FP32 TMEM
-//     accumulator per level every 512 k, levels 0..4 are summed exactly (below
-//     2^24 quanta); levels >= 5 share one accumulator.  After every 512 k the
-//     epilogue converts each level to an integer number of 2^-35 quanta
-//     (exactly for levels 0..4; the shared accumulator rounded to one
-//     quantum) and adds it into int64 register sums on the integer pipes, so
-//     the sum over K is exact up to that one rounding per chunk (K <= 8192
-//     keeps it below 2^63).  At the end it converts once to FP64, applies
-//     2^(e_i + f_j - 49) and the method's fused linear combinations, and
-//     writes FP64.
+//     2^(-7L), at most (L + 3) 2^12 of them per k.  Each level has its own
+//     FP32 TMEM accumulator, restarted every 512 k, so levels 0..5 are summed
+//     exactly (at most 2^24 quanta); levels 6 and 7 round far below FP64
+//     precision.  After every 512 k the epilogue converts each level to an
+//     integer number of 2^-35 quanta (exactly for levels 0..5) and adds it
+//     into int64 register sums on the integer pipes, so the sum over K is
+//     exact but for levels 6, 7 (K <= 8192 keeps it below 2^63).  At the end
+//     it converts once to FP64, applies 2^(e_i + f_j - 49) and the method's
+//     fused linear combinations, and writes FP64.
 //
 // The result has FP64-class accuracy (slices carry 57 bits of each row or
 // column maximum; the integer sums round once per 512 k) at a cost of
@@ -45,10 +44,13 @@
 // One CTA computes a 128 x 64 tile (S = 8):
 //   warp 0     TMA producer: all S slices of A (128 x 32) and of B^T (64 x 32)
 //              for one 32-wide k-block per stage, 64-byte swizzle, 2 stages;
-//   warp 1     allocates 512 TMEM columns (6 accumulators of 64 columns) and
-//              issues the MMAs (cta_group::1, M = 128, N = 64, K = 16),
-//              level by level, restarting each accumulator at a chunk start
-//              once the epilogue has read it;
+//   warp 1     allocates 512 TMEM columns (8 level accumulators of 64
+//              columns) and issues the MMAs (cta_group::1, M = 128, K = 16):
+//              per slice p of A, N = 128 instructions that pair the slices q,
+//              q + 1 of B into the accumulators of levels p + q, p + q + 1
+//              (16 per k-step, plus 4 of N = 64 for the odd pair left), the
+//              p = 0 instructions restarting every accumulator at a chunk
+//              start once the epilogue has read it;
 //   warps 2-9  two per TMEM lane quarter, 32 columns each: after each chunk,
 //              read every accumulator (freeing it at once), add it into the
 //              int64 sums, and at the end run the FP64 epilogue.
@@ -74,8 +76,7 @@ constexpr int BM = 128;
 constexpr int BN = 64;
 constexpr int BK = 32;                 // 32 bf16 = 64 bytes = one swizzle row
 constexpr int kChunkKb = 16;           // 16 k-blocks = 512 k per accumulator chunk
-constexpr int kExact = 5;              // levels with their own accumulator
-constexpr int kAcc = kExact + 1;       // plus one for the levels >= kExact
+constexpr int kAcc = S;               // one accumulator of BN columns per level p + q < S
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kCols = BN / 2;          // columns per epilogue warp
@@ -85,12 +86,19 @@ constexpr int kStageBytes = S * (kABytes + kBBytes);
 constexpr int kStages = 2;
 constexpr int kSmem = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
-static_assert(kAcc * BN <= (int)kTmemCols, "accumulators exceed TMEM");
+static_assert(kAcc * BN <= (int)kTmemCols, "TMEM columns");
 static_assert(kSmem <= 227 * 1024, "shared memory");
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// Instruction descriptors, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc =
+// An N = 2 BN instruction reads the B slices q and q + 1, which lie next to
+// each other along N in shared memory, and writes the accumulators of levels
+// p + q and p + q + 1, which lie next to each other in TMEM: two slice pairs
+// per instruction (a 128 x 64 x 16 MMA runs at 2/3 of the tensor peak on
+// GB300, 128 x 128 x 16 at the peak).
+constexpr uint32_t kIdesc1 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t kIdesc2 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 // Shared-memory descriptors (built in the MMA loop): K-major, 64-byte
 // swizzle, rows of 64 bytes, 8-row (512-byte) atoms stacked along M/N
@@ -106,7 +114,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       : "memory");
 }
 
-__host__ __device__ constexpr int acc_of(int level) { return level < kExact ? level : kExact; }
 
 // ------------------------------------------------------------- slicing ---
 // Exponent e with |x| * 2^-e < 1 for every x of the line: frexp of the max.
@@ -324,32 +331,39 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t a_lo = ((smem_u32(smem + st * kStageBytes) & 0x3FFFFu) >> 4) | (1u << 16);
           const uint32_t b_lo = a_lo + (uint32_t)((S * kABytes) >> 4);
-          const uint32_t restart_acc = kk == 0 ? 0u : 1u;  // fresh accumulators at a chunk start
+          const bool chunk_start = kk == 0;
           const bool wait_free = kk == 0 && c > 0;
           bool stop = false;
 #pragma unroll
-          for (int L = 0; L < S; ++L) {
-            // before an accumulator's first MMA of a chunk, wait until the
-            // epilogue has read it (previous chunk)
-            if (L <= kExact && wait_free) {
-              if (!mbar_wait(&free_bar[acc_of(L)], (c - 1) & 1, &abort_flag)) {
-                abort_flag = 1;
-                stop = true;
-                break;
-              }
-              tc_fence_after();
-            }
-            const uint32_t d = tmem + (uint32_t)(acc_of(L) * BN);
+          for (int j = 0; j < BK / 16 && !stop; ++j) {  // K = 16 bf16 (32 bytes) per instruction
 #pragma unroll
-            for (int p = 0; p <= L; ++p) {
-              const int q = L - p;
+            for (int p = 0; p < S; ++p) {
+              const uint64_t ad = ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
+              // pairs (p, q), (p, q + 1) for q = 0, 2, ...: levels p + q, p + q + 1 < S
 #pragma unroll
-              for (int j = 0; j < BK / 16; ++j) {  // K = 16 bf16 (32 bytes) per instruction
-                const uint64_t ad =
-                    ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
+              for (int q = 0; p + q + 1 < S; q += 2) {
                 const uint64_t bd =
                     ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
-                mma_bf16(d, ad, bd, kIdesc, (L <= kExact && p == 0 && j == 0) ? restart_acc : 1u);
+                // p = 0 touches every level first: there a chunk restarts its
+                // accumulators, after the epilogue has read them
+                const bool restart = chunk_start && j == 0 && p == 0;
+                if (restart && wait_free) {
+                  if (!mbar_wait(&free_bar[q], (c - 1) & 1, &abort_flag) ||
+                      !mbar_wait(&free_bar[q + 1], (c - 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                  }
+                  tc_fence_after();
+                }
+                mma_bf16(tmem + (uint32_t)((p + q) * BN), ad, bd, kIdesc2, restart ? 0u : 1u);
+              }
+              if (stop) break;
+              if ((S - p) & 1) {  // the last pair (p, S - 1 - p) alone, level S - 1
+                const int q = S - 1 - p;
+                const uint64_t bd =
+                    ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
+                mma_bf16(tmem + (uint32_t)((S - 1) * BN), ad, bd, kIdesc1, 1u);
               }
             }
           }
@@ -395,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&free_bar[a]);
-        const int e = a < kExact ? 7 * a : 35;                 // value * 2^e is an integer (or rounded to one)
+        const int e = 7 * a < 35 ? 7 * a : 35;  // value * 2^e is an integer (rounded for levels > 5)
         const float sc = __int_as_float((127 + e) << 23);
         const long long unit = 1LL << (35 - e);
 #pragma unroll

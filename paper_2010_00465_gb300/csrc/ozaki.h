@@ -11,7 +11,8 @@ namespace cs {
 #ifndef COSSIN_OZAKI_SLICES
 #define COSSIN_OZAKI_SLICES 8
 #endif
-// 7-bit slices per operand: 57 bits of each row / column maximum (8 slices)
+// 7-bit slices per operand: 57 bits of each row / column maximum (8 slices;
+// one 64-column TMEM accumulator per level, so at most 8)
 constexpr int kOzakiSlices = COSSIN_OZAKI_SLICES;
 
 constexpr int64_t kOzakiMaxK = 8192;  // inner dimension limit of the int64 sums
