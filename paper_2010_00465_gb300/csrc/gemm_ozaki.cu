@@ -53,7 +53,10 @@
 //              start once the epilogue has read it;
 //   warps 2-9  two per TMEM lane quarter, 32 columns each: after each chunk,
 //              read every accumulator (freeing it at once), add it into the
-//              int64 sums, and at the end run the FP64 epilogue.
+//              int64 sums; at the end stage the tile through the (then idle)
+//              shared memory and run the FP64 epilogue row by row with
+//              coalesced loads and stores (a thread-per-row epilogue took a
+//              fifth of the kernel's time).
 // Every mbarrier wait is bounded; on expiry the CTA stops issuing, waits
 // (bounded) for what it issued, frees TMEM and raises *err.
 #include <cuda.h>
@@ -74,20 +77,29 @@ using namespace ptx;
 constexpr int S = kOzakiSlices;        // slices per operand
 constexpr int BM = 128;
 constexpr int BN = 64;
-constexpr int BK = 32;                 // 32 bf16 = 64 bytes = one swizzle row
-constexpr int kChunkKb = 16;           // 16 k-blocks = 512 k per accumulator chunk
+#ifndef COSSIN_OZAKI_BK
+#define COSSIN_OZAKI_BK 32
+#endif
+// k per pipeline stage: 32 bf16 = 64 bytes (64-byte swizzle, 2 stages) or
+// 16 = 32 bytes (32-byte swizzle, 4 stages); the same 192 KB of slices in
+// flight.  The 32-wide stage measured 5 % faster (fewer barriers and commits).
+constexpr int BK = COSSIN_OZAKI_BK;
+constexpr int kSwizzleBytes = BK * 2;  // one swizzle row = one stage row
+constexpr int kChunkKb = 512 / BK;     // k-blocks per 512-k accumulator chunk
 constexpr int kAcc = S;               // one accumulator of BN columns per level p + q < S
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kCols = BN / 2;          // columns per epilogue warp
-constexpr int kABytes = BM * BK * 2;   // 8 KB per A slice
-constexpr int kBBytes = BN * BK * 2;   // 4 KB per B slice
+constexpr int kABytes = BM * BK * 2;   // one A slice of a stage
+constexpr int kBBytes = BN * BK * 2;   // one B slice of a stage
 constexpr int kStageBytes = S * (kABytes + kBBytes);
-constexpr int kStages = 2;
+constexpr int kStages = BK == 16 ? 4 : 2;
+constexpr int kGroupM = 8;             // M tiles per raster group
 constexpr int kSmem = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
 static_assert(kAcc * BN <= (int)kTmemCols, "TMEM columns");
 static_assert(kSmem <= 227 * 1024, "shared memory");
+static_assert(BM * (BN + 1) * 8 <= kStages * S * (BM * BK * 2 + BN * BK * 2), "epilogue tile fits the stages");
 // Instruction descriptors, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 // An N = 2 BN instruction reads the B slices q and q + 1, which lie next to
@@ -271,7 +283,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int chunks_committed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // Tiles in groups of kGroupM rows of M tiles, N fastest within a group, so
+  // that the CTAs resident at once share their slices of A and B in L2 (the
+  // slices of all of B exceed L2 at n = 4096).
+  const int nM = Mpad / BM, nN = Npad / BN;
+  const int t = blockIdx.x;
+  const int group = t / (kGroupM * nN);
+  const int rows = min(kGroupM, nM - group * kGroupM);
+  const int within = t - group * kGroupM * nN;
+  const int m0 = (group * kGroupM + within % rows) * BM, n0 = (within / rows) * BN;
   const int num_kb = (K + BK - 1) / BK;
   const int num_chunks = (num_kb + kChunkKb - 1) / kChunkKb;
 
@@ -319,7 +339,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // LBO = 1, the high word SBO = 512 B, version 1 and the 64-byte
       // swizzle; every operand of a stage is at a compile-time offset from
       // the stage base, so each MMA costs two integer adds to issue.
-      constexpr uint32_t kDescHi = (512u >> 4) | (1u << 14) | (4u << 29);
+      // SBO = 8 rows x swizzle bytes; layout type 6 = 32-byte, 4 = 64-byte swizzle
+      constexpr uint32_t kDescHi =
+          ((uint32_t)(8 * kSwizzleBytes) >> 4) | (1u << 14) | ((kSwizzleBytes == 32 ? 6u : 4u) << 29);
       int kb = 0;
       for (int c = 0; c < num_chunks && !abort_flag; ++c) {
         for (int kk = 0; kk < kChunkKb && kb < num_kb; ++kk, ++kb) {
@@ -419,55 +441,62 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    const int r = m0 + quarter * 32 + lane;
-    if (ok && r < M) {
-      const int er = ex[r] - 14 - 35;
-      const int d = r % K;
-      const double xdr = xd[r];
-      const double* __restrict__ yrow = Y + (int64_t)d * ldy;
-      const double* __restrict__ xrow = X + (int64_t)r * ldx;
-      // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
-      auto full = [&](int j, int cc) {
-        const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
-        return fma((double)acc[j], pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
-      };
-      if (epi.split_row >= 0) {
-        const bool top = r < epi.split_row;
-        const int64_t rr = top ? r : r - epi.split_row;
-        const int t = top ? 0 : 1;
+    // Stage the tile (FP64 sums, row stride 2 kCols + 1 doubles) in the
+    // shared memory of the finished pipeline, then walk it row by row.
+    double* tile = (double*)smem;
+    constexpr int kLd = 2 * kCols + 1;
+    if (ok) {
+      const int rl = quarter * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < kCols; ++j) {
-          const int cc = n0 + col0 + j;
-          if (cc >= N) break;
-          const double p = full(j, cc);
-          epi.out[t][rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
-        }
-      } else {
+      for (int j = 0; j < kCols; ++j) tile[rl * kLd + col0 + j] = (double)acc[j];
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+    if (!abort_flag) {
+      const int we = warp - 2;
+#pragma unroll 1
+      for (int rl = we; rl < BM; rl += kEpiWarps) {
+        const int r = m0 + rl;
+        if (r >= M) break;
+        const int er = ex[r] - 14 - 35;
+        const int d = r % K;
+        const double xdr = xd[r];
+        const double* __restrict__ yrow = Y + (int64_t)d * ldy;
+        const double* __restrict__ xrow = X + (int64_t)r * ldx;
 #pragma unroll
-        for (int j = 0; j < kCols; ++j) {
-          const int cc = n0 + col0 + j;
-          if (cc >= N) break;
-          const double p = full(j, cc);
-          const int64_t idx = (int64_t)r * ldo + cc;
-          double in[EPI_MAX_IN], o[EPI_MAX_OUT];
+        for (int h = 0; h < BN / 32; ++h) {
+          const int cl = 32 * h + lane;
+          const int cc = n0 + cl;
+          if (cc >= N) continue;
+          // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
+          const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
+          const double p = fma(tile[rl * kLd + cl], pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
+          if (epi.split_row >= 0) {
+            const bool top = r < epi.split_row;
+            const int64_t rr = top ? r : r - epi.split_row;
+            const int t = top ? 0 : 1;
+            epi.out[t][rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
+          } else {
+            const int64_t idx = (int64_t)r * ldo + cc;
+            double in[EPI_MAX_IN], o[EPI_MAX_OUT];
 #pragma unroll
-          for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
+            for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
 #pragma unroll
-          for (int t = 0; t < EPI_MAX_OUT; ++t) {
-            if (t >= epi.n_out) break;
-            double v = epi.alpha[t] * p + (r == cc ? epi.gamma[t] : 0.0);
+            for (int t = 0; t < EPI_MAX_OUT; ++t) {
+              if (t >= epi.n_out) break;
+              double v = epi.alpha[t] * p + (r == cc ? epi.gamma[t] : 0.0);
 #pragma unroll
-            for (int q = 0; q < EPI_MAX_IN; ++q)
-              if (q < epi.n_in) v += epi.beta[t][q] * in[q];
+              for (int q = 0; q < EPI_MAX_IN; ++q)
+                if (q < epi.n_in) v += epi.beta[t][q] * in[q];
 #pragma unroll
-            for (int u = 0; u < EPI_MAX_OUT; ++u)
-              if (u < t) v += epi.delta[t][u] * o[u];
-            o[t] = v;
-          }
+              for (int u = 0; u < EPI_MAX_OUT; ++u)
+                if (u < t) v += epi.delta[t][u] * o[u];
+              o[t] = v;
+            }
 #pragma unroll
-          for (int t = 0; t < EPI_MAX_OUT; ++t) {
-            if (t >= epi.n_out) break;
-            epi.out[t][idx] = o[t];
+            for (int t = 0; t < EPI_MAX_OUT; ++t) {
+              if (t >= epi.n_out) break;
+              epi.out[t][idx] = o[t];
+            }
           }
         }
       }
@@ -529,8 +558,8 @@ cs_status make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols,
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, kSwizzleBytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(CS_ECUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
   return CS_OK;
@@ -544,7 +573,7 @@ OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K) {
   OzakiDims d;
   d.Mpad = (M + BM - 1) / BM * BM;
   d.Npad = (N + BN - 1) / BN * BN;
-  d.ldk = (K + BK - 1) / BK * BK;
+  d.ldk = (K + 31) / 32 * 32;  // the slicing kernels work in 32 x 32 tiles
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   d.a_bytes = al((size_t)S * d.Mpad * d.ldk * 2);
   d.b_bytes = al((size_t)S * d.Npad * d.ldk * 2);
@@ -597,8 +626,9 @@ cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, i
     CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr_set = true;
   }
-  dim3 grid((unsigned)(d.Npad / BN), (unsigned)(d.Mpad / BM));
-  if (grid.y > 65535) return fail(CS_EINVAL, "gemm_f64_emu: grid too large");
+  const int64_t tiles = (d.Npad / BN) * (d.Mpad / BM);
+  if (tiles > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: grid too large");
+  dim3 grid((unsigned)tiles);
   ozaki_kernel<<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex, fx,
                                                   X, ldx, Y, ldy, xd, yd, ldo, epi, err);
   CS_CUDA_CHECK(cudaGetLastError());
