@@ -62,6 +62,7 @@ constexpr int kBBytes = BN * BK * 4;
 constexpr int kStageBytes = 2 * (kABytes + kBBytes);
 constexpr int kStages = 3;
 constexpr int kSmem = kStages * kStageBytes + 1024;
+static_assert(3 * BM * BN * 4 <= kStages * kStageBytes, "epilogue tiles fit the stages");
 #ifndef COSSIN_TC_GROUP
 #define COSSIN_TC_GROUP 1
 #endif
@@ -238,50 +239,65 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[b]);
     }
+    // The epilogue runs through shared memory (the pipeline stages are idle
+    // now): the tile P is staged row-per-thread, then walked row by row with
+    // coalesced input reads and row-major stores, while outputs that are
+    // also wanted transposed are staged again and written column by column.
+    // (The thread-per-row epilogue took up to 44 % of a CTA's time in the
+    // method's multi-output steps: its row-major accesses are uncoalesced.)
+    // Tiles are 128 x 128 floats with an XOR swizzle (column ^ (row & 31)),
+    // conflict-free for both access directions; tile 0 holds P and is reused
+    // by the first transposed output, tiles 1 and 2 take the next two.
+    float* tiles = (float*)smem;
+    auto sw = [](int rl, int cl) { return rl * BN + (cl ^ (rl & 31)); };
     if (ok) {
-      // sum = main (compensated) + corrections (accumulated over the whole K
-      // in TMEM columns 256..383, complete since the last group's commit),
-      // written back to TMEM columns 0..127 so the epilogue can walk it.
+      // sum = main (compensated) + corrections (accumulated over the whole
+      // K in TMEM columns 256..383, complete since the last group's commit)
       const uint32_t t_corr = tmem + lane_off + 256u + (uint32_t)col0;
+      const int rl = quarter * 32 + lane;
 #pragma unroll
       for (int c0 = 0; c0 < kHalf; c0 += 8) {
-        uint32_t vc[8], vk[8], v[8];
+        uint32_t vc[8], vk[8];
         tmem_ld8(t_corr + (uint32_t)c0, vc);
         tmem_ld8(t_comp + (uint32_t)c0, vk);
         tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          v[j] = __float_as_uint(acc_hi[c0 + j] + (__uint_as_float(vc[j]) - __uint_as_float(vk[j])));
-        tmem_st8(tmem + lane_off + (uint32_t)(col0 + c0), v);
+          tiles[sw(rl, col0 + c0 + j)] = acc_hi[c0 + j] + (__uint_as_float(vc[j]) - __uint_as_float(vk[j]));
       }
-      tmem_st_wait();
-      const int r = m0 + quarter * 32 + lane;
+    }
+    // transposed outputs staged in tiles 0..2 (more would be written directly)
+    int tslot[EPI_MAX_OUT];
+    int n_staged = 0;
+#pragma unroll
+    for (int t = 0; t < EPI_MAX_OUT; ++t) tslot[t] = (t < epi.n_out && epi.outT_hi[t] && n_staged < 3) ? n_staged++ : -1;
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+    const int we = warp - 2;
+    if (!abort_flag) {
 #pragma unroll 1
-      for (int c0 = col0; c0 < col0 + kHalf && n0 + c0 < N; c0 += 8) {
-        uint32_t v[8];
-        tmem_ld8(tmem + lane_off + (uint32_t)c0, v);
-        tmem_ld_wait();
-        if (r >= M) continue;
-        const int cbase = n0 + c0;
-        if (epi.split_row >= 0) {
-          const bool top = r < epi.split_row;
-          const int rr = top ? r : r - (int)epi.split_row;
-          const int t = top ? 0 : 1;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = cbase + j;
-            if (c >= N) break;
-            const float val = epi.alpha[t] * __uint_as_float(v[j]) + (rr == c ? epi.gamma[t] : 0.f);
+      for (int rl = we; rl < BM; rl += kEpiWarps) {
+        const int r = m0 + rl;
+        if (r >= M) break;
+#pragma unroll 1
+        for (int g = 0; g < BN / 32; ++g) {
+          const int cl = 32 * g + lane;
+          const int c = n0 + cl;
+          if (c >= N) continue;
+          const float p = tiles[sw(rl, cl)];
+          if (epi.split_row >= 0) {
+            const bool top = r < epi.split_row;
+            const int rr = top ? r : r - (int)epi.split_row;
+            const int t = top ? 0 : 1;
+            const float val = epi.alpha[t] * p + (rr == c ? epi.gamma[t] : 0.f);
             split_store(val, epi.out_hi[t], epi.out_lo[t], (int64_t)rr * ldo + c);
-            if (epi.outT_hi[t]) split_store(val, epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + rr);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = cbase + j;
-            if (c >= N) break;
+            if (epi.outT_hi[t]) {
+              if (tslot[t] >= 0)
+                tiles[tslot[t] * BM * BN + sw(rl, cl)] = val;
+              else
+                split_store(val, epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + rr);
+            }
+          } else {
             const int64_t idx = (int64_t)r * ldo + c;
-            const float p = __uint_as_float(v[j]);
             float in[EPI_MAX_IN], o[EPI_MAX_OUT];
 #pragma unroll
             for (int q = 0; q < EPI_MAX_IN; ++q) {
@@ -307,8 +323,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = 0; t < EPI_MAX_OUT; ++t) {
               if (t >= epi.n_out) break;
               split_store(o[t], epi.out_hi[t], epi.out_lo[t], idx);
-              if (epi.outT_hi[t]) split_store(o[t], epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + r);
+              if (epi.outT_hi[t]) {
+                if (tslot[t] >= 0)
+                  tiles[tslot[t] * BM * BN + sw(rl, cl)] = o[t];
+                else
+                  split_store(o[t], epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + r);
+              }
             }
+          }
+        }
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+    if (!abort_flag) {
+#pragma unroll 1
+      for (int t = 0; t < EPI_MAX_OUT; ++t) {
+        if (t >= epi.n_out || tslot[t] < 0) continue;
+        const float* tile = tiles + tslot[t] * BM * BN;
+#pragma unroll 1
+        for (int cl = we; cl < BN; cl += kEpiWarps) {
+          const int c = n0 + cl;
+          if (c >= N) break;
+#pragma unroll
+          for (int g = 0; g < BM / 32; ++g) {
+            const int rl = 32 * g + lane;
+            const int r = m0 + rl;
+            if (r >= M) continue;
+            // stacked mode: only output 0 (rows below split_row) is transposed
+            if (epi.split_row >= 0 && r >= epi.split_row) continue;
+            split_store(tile[sw(rl, cl)], epi.outT_hi[t], epi.outT_lo[t], (int64_t)c * ldo + r);
           }
         }
       }
