@@ -168,17 +168,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a_hi = smem_u32(smem + st * kStageBytes);
-          const uint32_t a_lo = a_hi + kABytes;
-          const uint32_t b_hi = a_hi + 2 * kABytes;
-          const uint32_t b_lo = b_hi + kBBytes;
+          // Descriptor words of desc_kmajor_sw128: the low word carries the
+          // start address (>> 4) and LBO = 1; every operand of the stage is at
+          // a compile-time offset from the stage base, so the per-MMA cost is
+          // one integer add (the issuing thread is otherwise the bottleneck).
+          constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);
+          const uint32_t base = ((smem_u32(smem + st * kStageBytes) & 0x3FFFFu) >> 4) | (1u << 16);
+          auto desc = [&](uint32_t byte_off) { return ((uint64_t)kDescHi << 32) | (uint64_t)(base + (byte_off >> 4)); };
+          const uint32_t fresh_main = kk != 0, fresh_corr = kb != 0;
 #pragma unroll
           for (int j = 0; j < BK / 8; ++j) {  // K = 8 tf32 (32 bytes) per instruction
             const uint32_t off = 32u * j;
-            const uint64_t ah = desc_kmajor_sw128(a_hi + off), al = desc_kmajor_sw128(a_lo + off);
-            const uint64_t bh = desc_kmajor_sw128(b_hi + off), bl = desc_kmajor_sw128(b_lo + off);
-            mma_tf32(d_main, ah, bh, kIdesc, (kk | j) != 0);  // fresh every group
-            mma_tf32(d_corr, al, bh, kIdesc, (kb | j) != 0);  // whole K
+            const uint64_t ah = desc(off), al = desc(kABytes + off);
+            const uint64_t bh = desc(2 * kABytes + off), bl = desc(2 * kABytes + kBBytes + off);
+            mma_tf32(d_main, ah, bh, kIdesc, j ? 1u : fresh_main);  // fresh every group
+            mma_tf32(d_corr, al, bh, kIdesc, j ? 1u : fresh_corr);  // whole K
             mma_tf32(d_corr, ah, bl, kIdesc, 1);
             if (COSSIN_TC_PASSES == 4) mma_tf32(d_corr, al, bl, kIdesc, 1);
           }
