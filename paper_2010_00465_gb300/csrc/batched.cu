@@ -191,8 +191,8 @@ __device__ void cta_product(const float* __restrict__ X, const float* __restrict
           buf ^= 1;
         }
       }
-#pragma unroll 1
-      for (int i = 0; i < R; ++i) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {  // unrolled: acc[i][j] stays in registers
         const int r = m0 + (i < H ? ty * H + i : T / 2 + ty * H + (i - H));
         if (r >= M) continue;
 #pragma unroll
@@ -233,8 +233,8 @@ __device__ void cta_product(const float* __restrict__ X, const float* __restrict
 }
 
 // T is the tile edge for orders above 64; orders <= 64 always use 64-wide tiles.
-template <int T>
-__global__ void __launch_bounds__(kThreads, T == 128 ? 1 : 2) batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order,
+template <int T, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order,
                                                            int count, int* queue, float* ws_all, int64_t ws_per_cta,
                                                            cs_info* infos, int32_t* status) {
   __shared__ __align__(16) float panels[4 * kBK * (T + 4)];
@@ -313,7 +313,10 @@ struct Variant {
   int tile;
   int ctas_per_sm;
 };
-const Variant kVariants[] = {{128, 1}, {64, 2}, {64, 1}};
+// {64, 4} compiles with 64 registers per thread to fit 32 warps per SM; the
+// autotuner keeps whichever variant is fastest on the batch.  (A 128-wide
+// tile at 2 CTAs per SM would spill 3 KB per thread.)
+const Variant kVariants[] = {{128, 1}, {64, 2}, {64, 1}, {64, 4}};
 
 std::mutex g_mu;
 bool g_plans_uploaded[64] = {};
@@ -403,9 +406,11 @@ cs_status launch_variant(int v, const BLayout& L, char* ws, int count, cs_info* 
   const int* order = (const int*)(ws + L.order);
   float* scratch = (float*)(ws + L.scratch);
   if (V.tile == 128)
-    batched_kernel<128><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
+    batched_kernel<128, 1><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
+  else if (V.ctas_per_sm >= 4)
+    batched_kernel<64, 4><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
   else
-    batched_kernel<64><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
+    batched_kernel<64, 2><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
