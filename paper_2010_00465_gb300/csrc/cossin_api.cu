@@ -499,9 +499,7 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
 
-// c(t^2 A), s(t, A) of Sec. 2.2 (see cs_spec); info->m is the family index.
-cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
-                  int32_t force_f, int32_t force_s, cs_info* info, cudaStream_t stream) {
+cs_status cs_check_args(int64_t n, double t, cs_prec prec, int32_t force_f, int32_t force_s) {
   CS_CHECK(check_prec(prec));
   if (n < 0 || n > kMaxN) return fail(CS_EINVAL, "n out of range [0, 65536]");
   if (uses_emu(prec) && n > kOzakiMaxK) return fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
@@ -509,6 +507,13 @@ cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, voi
   if ((force_f == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_family and force_sigma must both be -1 or both set");
   if (force_f < -1 || force_f > 3) return fail(CS_EINVAL, "force_family must be in [0, 3]");
   if (force_s < -1 || force_s > kMaxS) return fail(CS_EINVAL, "force_sigma must be in [0, 64]");
+  return CS_OK;
+}
+
+// c(t^2 A), s(t, A) of Sec. 2.2 (see cs_spec); info->m is the family index.
+cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
+                  int32_t force_f, int32_t force_s, cs_info* info, cudaStream_t stream) {
+  CS_CHECK(cs_check_args(n, t, prec, force_f, force_s));
   const int table = (prec == CS_FP64 || prec == CS_FP64_EMU) ? 0 : 1;
   if (n == 0) {
     if (info) *info = cs_info{0.0, force_f == -1 ? 0 : force_f, force_s == -1 ? 0 : force_s, 0, table, 0.0};
@@ -650,9 +655,7 @@ cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, v
                     int32_t force_family, int32_t force_sigma, cs_info* info, cossin_stream_t stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (ws) return cs::cs_impl(A, n, t, prec, C, S, ws, ws_bytes, force_family, force_sigma, info, st);
-  CS_CHECK(cs::check_prec(prec));
-  if (n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "n out of range [0, 65536]");
-  if (cs::uses_emu(prec) && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
+  CS_CHECK(cs::cs_check_args(n, t, prec, force_family, force_sigma));
   if (n == 0) return cs::cs_impl(A, n, t, prec, C, S, nullptr, 0, force_family, force_sigma, info, st);
   const size_t bytes = cs::make_layout(n, prec).total;
   void* buf = nullptr;

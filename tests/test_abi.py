@@ -95,3 +95,37 @@ def test_library_has_no_cpu_fallback_symbols(L):
     import subprocess
     out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
     assert "oracle" not in out
+
+
+def test_emulated_precisions_host_checks(L):
+    """The emulated-FP64 precisions add their slice scratch to the workspace
+    and accept n <= 8192 only (the int64 level sums), refused before any
+    device work."""
+    for p in ("fp64_emu", "split_emu"):
+        assert api.workspace_size(1024, p) > api.workspace_size(1024, "fp64" if p == "fp64_emu" else "split_tf32")
+        assert api.workspace_size(8192, p) > 0
+        with pytest.raises(_lib.CossinError) as e:
+            api.workspace_size(8193, p)
+        assert e.value.status == _lib.CS_EINVAL
+    assert api.workspace_size(8193, "fp64") > 0
+    assert api.unitary_workspace_size(100, "fp64") > api.workspace_size(100, "fp64")
+    with pytest.raises(_lib.CossinError):
+        api.workspace_size(16, 5)
+
+
+def test_cs_and_unitary_argument_errors_before_any_gpu_work(L):
+    nul = ctypes.c_void_p(0)
+    info = _lib.CsInfo()
+    cs = L.cossin_cs
+    assert cs(nul, 4, float("nan"), 0, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert cs(nul, 4, 1.0, 0, nul, nul, nul, 0, 4, 0, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert cs(nul, 4, 1.0, 0, nul, nul, nul, 0, 1, -1, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert cs(nul, 4, 1.0, 0, nul, nul, nul, 0, 1, 65, ctypes.byref(info), nul) == _lib.CS_EINVAL
+    assert cs(nul, 0, 1.0, 0, nul, nul, nul, 0, 2, 3, ctypes.byref(info), nul) == _lib.CS_OK
+    assert (info.m, info.s, info.products) == (2, 3, 0)
+    un = L.cossin_unitary
+    assert un(nul, 4, float("inf"), 0, nul, nul, 0, -1, -1, None, nul) == _lib.CS_EINVAL
+    assert un(nul, 0, 1.0, 0, nul, nul, 0, -1, -1, None, nul) == _lib.CS_OK
+    ub = L.cossin_unitary_backward
+    assert ub(0, 4, 1.0, nul, nul, nul, nul, -1, -1, nul, nul) == _lib.CS_OK
+    assert ub(1, 4, float("nan"), nul, nul, nul, nul, -1, -1, nul, nul) == _lib.CS_EINVAL
