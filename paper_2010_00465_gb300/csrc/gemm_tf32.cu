@@ -222,26 +222,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t t_main = tmem + lane_off + 128u * b + (uint32_t)col0;
+      // Read the whole main buffer first and release it to the MMA warp at
+      // once; the compensated sums (TMEM columns 384..511, touched by the
+      // epilogue only) are updated afterwards, off the MMA warp's path.
+      uint32_t vm[kHalf / 8][8];
 #pragma unroll
-      for (int c0 = 0; c0 < kHalf; c0 += 8) {
-        uint32_t vm[8], vc[8];
-        tmem_ld8(t_main + (uint32_t)c0, vm);
-        if (g > 0) tmem_ld8(t_comp + (uint32_t)c0, vc);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float lo = g > 0 ? __uint_as_float(vc[j]) : 0.f;
-          const float y = __uint_as_float(vm[j]) - lo;
-          const float t = acc_hi[c0 + j] + y;
-          vc[j] = __float_as_uint((t - acc_hi[c0 + j]) - y);
-          acc_hi[c0 + j] = t;
-        }
-        tmem_st8(t_comp + (uint32_t)c0, vc);
-      }
-      tmem_st_wait();
+      for (int i = 0; i < kHalf / 8; ++i) tmem_ld8(t_main + (uint32_t)(8 * i), vm[i]);
+      tmem_ld_wait();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[b]);
+#pragma unroll
+      for (int i = 0; i < kHalf / 8; ++i) {
+        uint32_t vc[8];
+        if (g > 0) {
+          tmem_ld8(t_comp + (uint32_t)(8 * i), vc);
+          tmem_ld_wait();
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = 8 * i + j;
+          const float lo = g > 0 ? __uint_as_float(vc[j]) : 0.f;
+          const float y = __uint_as_float(vm[i][j]) - lo;
+          const float t = acc_hi[c] + y;
+          vc[j] = __float_as_uint((t - acc_hi[c]) - y);
+          acc_hi[c] = t;
+        }
+        tmem_st8(t_comp + (uint32_t)(8 * i), vc);
+      }
+      tmem_st_wait();
     }
     // The epilogue runs through shared memory (the pipeline stages are idle
     // now): the tile P is staged row-per-thread, then walked row by row with
