@@ -65,7 +65,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+        # raw samples (the JSON line carries their summary); COSSIN_CLOCK_LOG_DIR
+        # chooses where they go
+        log_dir = os.environ.get("COSSIN_CLOCK_LOG_DIR", os.path.join(ROOT, "_clocks"))
+        self.path = os.path.join(log_dir, "clocks_rank%d.csv" % gpu_index)
 
     def __enter__(self):
         try:
@@ -286,7 +289,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "+".join("f64" if p == "fp64" else "f32(3xtf32)" for p in precs),
+        "scaling": "weak", "vs_baseline": None, "dtype": "+".join("f64" if p == "fp64" else "f32(4xtf32)" for p in precs),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "precisions": precs, "matrices_per_step": len(work),
                    "l2": "inputs > L2: each step reads %d matrices of %d MB and streams GBs of workspace"

@@ -59,7 +59,7 @@ typedef enum {
    * accumulation (promoted, compensated), linear combinations in FP32. */
   CS_FP32 = 1,
   /* FP64 in and out; single table; the Taylor chain (steps 3-4) as
-   * three-pass TF32 tensor-core products, while the norm, the choice of
+   * four-pass TF32 tensor-core products, while the norm, the choice of
    * (m, s) and the double-angle steps run in FP64.  Accuracy is FP32-level. */
   CS_SPLIT_TF32 = 2,
   /* FP64 in and out; double table; every product emulated on the BF16
@@ -279,7 +279,7 @@ cs_status cossin_device_status(cossin_stream_t stream);
 typedef enum {
   CS_KERNEL_NORM1 = 0,      /* bytes = n^2 * element size */
   CS_KERNEL_GEMM_F64 = 1,   /* flops = 2 M N K */
-  CS_KERNEL_GEMM_TF32 = 2,  /* flops = 2 M N K (algorithmic, not the 3 passes) */
+  CS_KERNEL_GEMM_TF32 = 2,  /* flops = 2 M N K (algorithmic, not the 4 passes) */
   CS_KERNEL_BATCHED = 3,    /* flops = sum over matrices of 2 n^3 (Pi_2m + 2 s) */
   CS_KERNEL_ADJOINT = 4,    /* flops = 2 M N K of the reverse-pass products */
   CS_KERNEL_OTHER = 5,      /* splits and conversions; bytes moved */

@@ -1,4 +1,4 @@
-// gemm_tf32.cu -- three-pass TF32 tensor-core product on tcgen05/TMEM with
+// gemm_tf32.cu -- four-pass TF32 tensor-core product on tcgen05/TMEM with
 // TMA-fed operands and the method's linear combinations fused in the epilogue.
 //
 // FP32 accuracy from TF32 tensor cores: every matrix is held as a pair

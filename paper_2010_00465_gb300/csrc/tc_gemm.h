@@ -1,4 +1,4 @@
-// tc_gemm.h -- the three-pass TF32 tensor-core product and its helpers.
+// tc_gemm.h -- the four-pass TF32 tensor-core product and its helpers.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -1,4 +1,4 @@
-// tf32_path.cu -- executor of the product plans on the three-pass TF32
+// tf32_path.cu -- executor of the product plans on the four-pass TF32
 // tensor-core kernel: the FP32 path (everything on tensor cores) and the
 // split-precision path (Taylor chain on tensor cores, double-angle steps in FP64).
 #include <stdlib.h>

@@ -1,6 +1,6 @@
 """Parity of the tensor-core paths with the FP64 oracle.
 
-CS_FP32: FP32 in/out, single table, every product a three-pass TF32 tcgen05
+CS_FP32: FP32 in/out, single table, every product a four-pass TF32 tcgen05
 product; CS_SPLIT_TF32: FP64 in/out, single table, Taylor chain on tensor
 cores, double-angle steps in FP64.  Both are compared with the oracle run on
 the same input (FP32 inputs upcast exactly) at the same (2m, s) with the single
