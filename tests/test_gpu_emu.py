@@ -171,3 +171,26 @@ def test_cs_and_unitary_forms():
     Uo, _ = oracle.unitary(A, 0.8)
     Ug = api.unitary(dev(A), 0.8, "fp64_emu")
     assert relfro(Ug.cpu().numpy(), Uo) <= TOL64
+
+
+@pytest.mark.parametrize("nrm", [1.0, 64.0])
+def test_n8192_block_diagonal(nrm):
+    """The largest order the emulated products accept (K = 8192): a permuted
+    block-diagonal matrix, sampled 64-blocks against the oracle."""
+    n, block = 8192, 64
+    g = inputs.rng(203)
+    perm = g.permutation(n)
+    A = np.zeros((n, n))
+    blocks = [inputs.matrix(block, "normal", nrm, index=203, sub=i) for i in range(n // block)]
+    for i, B in enumerate(blocks):
+        idx = perm[i * block:(i + 1) * block]
+        A[np.ix_(idx, idx)] = B
+    C, S, info = api.cossin(dev(A), "fp64_emu", return_info=True)
+    assert (info["m"], info["s"]) == oracle.select(oracle.norm1(A), "double")
+    C = C.cpu().numpy()
+    S = S.cpu().numpy()
+    for i in list(range(0, n // block, 29)) + [n // block - 1]:
+        idx = perm[i * block:(i + 1) * block]
+        Co, So, _ = oracle.cossin(A[np.ix_(idx, idx)], m=info["m"], s=info["s"])
+        assert relfro(C[np.ix_(idx, idx)], Co) <= TOL64
+        assert relfro(S[np.ix_(idx, idx)], So) <= TOL64

@@ -197,3 +197,19 @@ def test_full_size_dense_properties(prec, family, nrm):
         w, V = torch.linalg.eigh(Ad)
         Cr = (V * torch.cos(w)) @ V.T
         assert float((Cd - Cr).norm() / Cr.norm()) <= TOL32
+
+
+@pytest.mark.parametrize("prec", ["split_tf32", "split_emu"])
+@pytest.mark.parametrize("nrm", [1.0, 64.0])
+def test_split_n8192_block_diagonal(prec, nrm):
+    """The split workload's larger order, n = 8192: a permuted block-diagonal
+    matrix, sampled 64-blocks against the oracle at the same (2m, s)."""
+    n, block = 8192, 64
+    A, blocks, perm = _block_case(n, block, nrm, index=67)
+    C, S, info = run(A, prec)
+    assert (info["m"], info["s"]) == oracle.select(oracle.norm1(A), "single")
+    for i in list(range(0, len(blocks), 23)) + [len(blocks) - 1]:
+        idx = perm[i * block:(i + 1) * block]
+        Co, So, _ = oracle.cossin(A[np.ix_(idx, idx)], "single", m=info["m"], s=info["s"])
+        assert relfro(C[np.ix_(idx, idx)], Co) <= TOL32
+        assert relfro(S[np.ix_(idx, idx)], So) <= TOL32
