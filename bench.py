@@ -428,27 +428,35 @@ def cs_form(api, wsp):
 def adjoint_form(api, count=512, n=128, reps=3):
     """The control workload: 512 FP64 matrices n = 128, A = H0 + sum u_k H_k,
     random cotangents; one batched backward call (forward recomputed with its
-    tape, then the reverse pass).  Work = 2 n^3 (3 Pi_2m + 6 s) per matrix."""
+    tape, then the reverse pass), with native and with emulated FP64
+    products.  Work = 2 n^3 (3 Pi_2m + 6 s) per matrix."""
     import torch
     import oracle
     from paper_2010_00465_gb300 import inputs
     A, GC, GS = inputs.hamiltonian_batch(count, n)
     Ad, GCd, GSd = (torch.from_numpy(x).cuda() for x in (A, GC, GS))
-    api.cossin_backward(Ad, GCd, GSd)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        dA, infos = api.cossin_backward(Ad, GCd, GSd, return_info=True)
-    torch.cuda.synchronize()
-    sec = (time.perf_counter() - t0) / reps
-    flops = sum(i["flops"] for i in infos)
-    b = 7
-    m, s = infos[b]["m"], infos[b]["s"]
-    ref = oracle.gradient(A[b], GC[b], GS[b], m, s)
-    err = float(np.linalg.norm(dA[b].cpu().numpy() - ref) / np.linalg.norm(ref))
-    pairs = sorted({(i["m"], i["s"]) for i in infos})
-    return {"count": count, "n": n, "ms_per_call": sec * 1e3, "alg_tflops": flops / sec / 1e12,
-            "ms_pairs": pairs, "rel_err_vs_oracle_block_frechet_matrix7": err}
+    out = {"count": count, "n": n}
+    res = {}
+    for prec in ("fp64", "fp64_emu"):
+        api.cossin_backward(Ad, GCd, GSd, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            dA, infos = api.cossin_backward(Ad, GCd, GSd, return_info=True, prec=prec)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / reps
+        flops = sum(i["flops"] for i in infos)
+        b = 7
+        m, s = infos[b]["m"], infos[b]["s"]
+        ref = oracle.gradient(A[b], GC[b], GS[b], m, s)
+        err = float(np.linalg.norm(dA[b].cpu().numpy() - ref) / np.linalg.norm(ref))
+        res[prec] = {"ms_per_call": sec * 1e3, "alg_tflops": flops / sec / 1e12,
+                     "rel_err_vs_oracle_block_frechet_matrix7": err}
+        out["ms_pairs"] = sorted({(i["m"], i["s"]) for i in infos})
+    out.update(res["fp64"])
+    out["fp64_emu"] = res["fp64_emu"]
+    out["fp64_emu"]["speedup_vs_fp64"] = res["fp64"]["ms_per_call"] / res["fp64_emu"]["ms_per_call"]
+    return out
 
 
 def batched_form(api, count=20000, reps=5, fp64_sample=240):

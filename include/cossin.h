@@ -196,6 +196,14 @@ cs_status cossin_backward(int64_t count, int64_t n, const double* A_dev, const d
                           const double* G_S_dev, double* dA_dev, double* C_dev, double* S_dev,
                           int32_t force_m, int32_t force_s, cs_info* infos_host, cossin_stream_t stream);
 
+/* As cossin_backward, with the FP64 products of the forward and reverse
+ * passes computed natively (prec = CS_FP64) or emulated on the BF16 tensor
+ * cores (prec = CS_FP64_EMU, n <= 8192; see CS_FP64_EMU).  Any other prec
+ * gives CS_EINVAL. */
+cs_status cossin_backward_ex(int64_t count, int64_t n, const double* A_dev, const double* G_C_dev,
+                             const double* G_S_dev, double* dA_dev, double* C_dev, double* S_dev, int32_t force_m,
+                             int32_t force_s, cs_prec prec, cs_info* infos_host, cossin_stream_t stream);
+
 /* ------------------------------------------------------------ unitary ---
  * The propagator U = e^{-itA} = cos(tA) - i sin(tA) of a real n x n matrix
  * (Sec. 1, the Schroedinger case: unitary when A is symmetric), by the

@@ -49,6 +49,8 @@ SIGNATURES = {
                                  ctypes.POINTER(CsInfo), _vp]),
     "cossin_matmul": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "cossin_backward": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "cossin_backward_ex": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int, _vp,
+                                          _vp]),
     "cossin_unitary_workspace_size": (ctypes.c_int, [_i64, ctypes.c_int, ctypes.POINTER(_sz)]),
     "cossin_unitary": (ctypes.c_int, [_vp, _i64, ctypes.c_double, ctypes.c_int, _vp, _vp, _sz, _i32, _i32,
                                       ctypes.POINTER(CsInfo), _vp]),

@@ -155,9 +155,11 @@ def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Te
 
 
 def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m: int | None = None,
-                    s: int | None = None, want_forward: bool = False, stream=None, return_info: bool = False):
+                    s: int | None = None, want_forward: bool = False, stream=None, return_info: bool = False,
+                    prec: str = "fp64"):
     """Gradient of <G_C, cos(A)> + <G_S, sin(A)> (FP64; A is n x n or a
-    [count, n, n] batch), at the (2m, s) the forward pass uses."""
+    [count, n, n] batch), at the (2m, s) the forward pass uses.  ``prec``
+    "fp64_emu" emulates the FP64 products on the BF16 tensor cores."""
     import numpy as np
     if A.dtype != torch.float64 or G_C.dtype != torch.float64 or G_S.dtype != torch.float64:
         raise TypeError("the adjoint runs in FP64")
@@ -180,11 +182,11 @@ def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m:
     infos = (CsInfo * max(count, 1))()
     fm = -1 if m is None else int(m)
     fs = -1 if s is None else int(s)
-    check(lib().cossin_backward(count, n, ctypes.c_void_p(A3.data_ptr()), ctypes.c_void_p(GC3.data_ptr()),
-                                ctypes.c_void_p(GS3.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
-                                ctypes.c_void_p(C.data_ptr() if C is not None else 0),
-                                ctypes.c_void_p(S.data_ptr() if S is not None else 0), fm, fs, infos,
-                                _stream_ptr(stream)))
+    check(lib().cossin_backward_ex(count, n, ctypes.c_void_p(A3.data_ptr()), ctypes.c_void_p(GC3.data_ptr()),
+                                   ctypes.c_void_p(GS3.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
+                                   ctypes.c_void_p(C.data_ptr() if C is not None else 0),
+                                   ctypes.c_void_p(S.data_ptr() if S is not None else 0), fm, fs, _prec(prec),
+                                   infos, _stream_ptr(stream)))
     if not batched:
         dA = dA[0]
         C = C[0] if C is not None else None

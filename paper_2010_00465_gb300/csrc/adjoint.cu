@@ -23,7 +23,9 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "ozaki.h"
 #include "plan.h"
+#include "tc_gemm.h"
 #include "theta_table.cuh"
 
 namespace cs {
@@ -89,6 +91,31 @@ __global__ void scatter_kernel(const double* __restrict__ src, double* __restric
 
 int blocks_for(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256, 152 * 8); }
 
+// The batched FP64 products of the forward and reverse passes: native, or
+// emulated on the BF16 tensor cores (gemm_f64_emu_batched, which takes its
+// operands untransposed: a transposed operand is materialised first).
+struct AdjProd {
+  bool emu = false;
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  double* tbuf[2] = {};
+  int* err = nullptr;
+  cs_status operator()(const double* X, bool tX, const double* Y, bool tY, const Epilogue<double>& e, int64_t n,
+                       int64_t g, cudaStream_t st) const {
+    const int64_t n2 = n * n;
+    if (!emu) return gemm_f64(X, Y, n, n, n, n, n, tX, tY, e, n, g, n2, n2, n2, st);
+    if (tX) {
+      CS_CHECK(transpose_f64_batched(X, tbuf[0], n, g, n2, st));
+      X = tbuf[0];
+    }
+    if (tY) {
+      CS_CHECK(transpose_f64_batched(Y, tbuf[1], n, g, n2, st));
+      Y = tbuf[1];
+    }
+    return gemm_f64_emu_batched(X, Y, n, n, n, n, n, e, n, g, n2, n2, n2, work, work_bytes, err, st);
+  }
+};
+
 // Write-once form of a plan: value ids for every step output.
 struct SsaStep {
   int X, Y;                 // value ids of the operands
@@ -142,8 +169,8 @@ Ssa make_ssa(int m, int s, double scale) {
 }
 
 // Accumulating product: Acc += op(X) op(Y), batched with stride n^2.
-cs_status gemm_acc(const double* X, bool tX, const double* Y, bool tY, double* Acc, double scale, int64_t n,
-                   int64_t batch, cudaStream_t stream) {
+cs_status gemm_acc(const AdjProd& prod, const double* X, bool tX, const double* Y, bool tY, double* Acc,
+                   double scale, int64_t n, int64_t batch, cudaStream_t stream) {
   Epilogue<double> e;
   e.n_in = 1;
   e.in[0] = Acc;
@@ -151,12 +178,11 @@ cs_status gemm_acc(const double* X, bool tX, const double* Y, bool tY, double* A
   e.out[0] = Acc;
   e.alpha[0] = scale;
   e.beta[0][0] = 1.0;
-  const int64_t n2 = n * n;
-  return gemm_f64(X, Y, n, n, n, n, n, tX, tY, e, n, batch, n2, n2, n2, stream);
+  return prod(X, tX, Y, tY, e, n, batch, stream);
 }
 
 cs_status run_group(const double* A, const double* GC, const double* GS, double* dA, double* C_out, double* S_out,
-                    int64_t n, int m, int s, int64_t g, double scale, cudaStream_t stream) {
+                    int64_t n, int m, int s, int64_t g, double scale, const AdjProd& prod, cudaStream_t stream) {
   const Ssa ssa = make_ssa(m, s, scale);
   const int64_t n2 = n * n;
   const int nlev = s + 1;
@@ -183,7 +209,7 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
     Epilogue<double> e = q.coef;
     for (int k = 0; k < e.n_in; ++k) e.in[k] = val(q.in[k]);
     for (int t = 0; t < e.n_out; ++t) e.out[t] = val(q.out[t]);
-    rc = gemm_f64(val(q.X), val(q.Y), n, n, n, n, n, false, false, e, n, g, n2, n2, n2, stream);
+    rc = prod(val(q.X), false, val(q.Y), false, e, n, g, stream);
   }
   for (int j = 0; rc == CS_OK && j < s; ++j) {
     Epilogue<double> ec;
@@ -191,13 +217,13 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
     ec.out[0] = val(levC(j + 1));
     ec.alpha[0] = 2.0;
     ec.gamma[0] = -1.0;
-    rc = gemm_f64(val(levC(j)), val(levC(j)), n, n, n, n, n, false, false, ec, n, g, n2, n2, n2, stream);
+    rc = prod(val(levC(j)), false, val(levC(j)), false, ec, n, g, stream);
     if (rc != CS_OK) break;
     Epilogue<double> es;
     es.n_out = 1;
     es.out[0] = val(levS(j + 1));
     es.alpha[0] = 2.0;
-    rc = gemm_f64(val(levS(j)), val(levC(j)), n, n, n, n, n, false, false, es, n, g, n2, n2, n2, stream);
+    rc = prod(val(levS(j)), false, val(levC(j)), false, es, n, g, stream);
   }
   if (rc == CS_OK && C_out) ce = cudaMemcpyAsync(C_out, val(levC(s)), per, cudaMemcpyDeviceToDevice, stream);
   if (rc == CS_OK && S_out && ce == cudaSuccess) ce = cudaMemcpyAsync(S_out, val(levS(s)), per, cudaMemcpyDeviceToDevice, stream);
@@ -213,10 +239,10 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
     const double* Sh = adj(levS(j + 1));
     double* Cj = adj(levC(j));
     double* Sj = adj(levS(j));
-    rc = gemm_acc(Ch, false, C, true, Cj, 2.0, n, g, stream);                  // 2 C'^ C^T
-    if (rc == CS_OK) rc = gemm_acc(C, true, Ch, false, Cj, 2.0, n, g, stream);  // 2 C^T C'^
-    if (rc == CS_OK) rc = gemm_acc(S, true, Sh, false, Cj, 2.0, n, g, stream);  // 2 S^T S'^
-    if (rc == CS_OK) rc = gemm_acc(Sh, false, C, true, Sj, 2.0, n, g, stream);  // 2 S'^ C^T
+    rc = gemm_acc(prod, Ch, false, C, true, Cj, 2.0, n, g, stream);                  // 2 C'^ C^T
+    if (rc == CS_OK) rc = gemm_acc(prod, C, true, Ch, false, Cj, 2.0, n, g, stream);  // 2 C^T C'^
+    if (rc == CS_OK) rc = gemm_acc(prod, S, true, Sh, false, Cj, 2.0, n, g, stream);  // 2 S^T S'^
+    if (rc == CS_OK) rc = gemm_acc(prod, Sh, false, C, true, Sj, 2.0, n, g, stream);  // 2 S'^ C^T
   }
   for (int i = (int)ssa.steps.size() - 1; rc == CS_OK && i >= 0; --i) {
     const SsaStep& q = ssa.steps[i];
@@ -238,8 +264,8 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
       rc = cuda_fail(ce, "epilogue_adjoint");
       break;
     }
-    rc = gemm_acc(phat, false, val(q.Y), true, adj(q.X), 1.0, n, g, stream);            // X^ += P^ Y^T
-    if (rc == CS_OK) rc = gemm_acc(val(q.X), true, phat, false, adj(q.Y), 1.0, n, g, stream);  // Y^ += X^T P^
+    rc = gemm_acc(prod, phat, false, val(q.Y), true, adj(q.X), 1.0, n, g, stream);            // X^ += P^ Y^T
+    if (rc == CS_OK) rc = gemm_acc(prod, val(q.X), true, phat, false, adj(q.Y), 1.0, n, g, stream);  // Y^ += X^T P^
   }
   if (rc == CS_OK) ce = cudaMemcpyAsync(dA, adj(ssa.A), per, cudaMemcpyDeviceToDevice, stream);
   if (rc == CS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
@@ -255,8 +281,9 @@ int64_t adjoint_products(int m, int s) { return 3 * products_of(m) + 6 * s; }
 // scale sits in the plans' coefficients, so the reverse pass carries it.
 cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A, const double* G_C,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
-                        cs_info* infos_host, cudaStream_t st) {
+                        cs_info* infos_host, cudaStream_t st, bool emu) {
   if (count < 0 || n < 0 || n > kMaxN) return fail(CS_EINVAL, "count or n out of range");
+  if (emu && n > kOzakiMaxK) return fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (!isfinite(scale)) return fail(CS_EINVAL, "t must be finite");
   if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");
   if (force_m != -1 && products_of(force_m) < 0) return fail(CS_EINVAL, "force_m must be 4, 8, 9, 16 or 24");
@@ -327,7 +354,24 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
       ce = cudaGetLastError();
       if (ce != cudaSuccess) rc = cuda_fail(ce, "gather");
     }
-    if (rc == CS_OK) rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, scale, st);
+    AdjProd prod;
+    char* eb = nullptr;
+    if (rc == CS_OK && emu) {
+      prod.emu = true;
+      prod.err = tc_error_word();
+      prod.work_bytes = ozaki_dims(n, n, n, g).total;
+      const size_t tb = sizeof(double) * (size_t)n2 * (size_t)g;
+      ce = cudaMallocAsync((void**)&eb, prod.work_bytes + 2 * tb, st);
+      if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaMallocAsync");
+      if (!prod.err) rc = fail(CS_ECUDA, "cannot resolve the device error word");
+      if (rc == CS_OK) {
+        prod.work = eb;
+        prod.tbuf[0] = (double*)(eb + prod.work_bytes);
+        prod.tbuf[1] = (double*)(eb + prod.work_bytes + tb);
+      }
+    }
+    if (rc == CS_OK) rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, scale, prod, st);
+    if (eb) cudaFreeAsync(eb, st);
     if (rc == CS_OK) {
       scatter_kernel<<<nb, 256, 0, st>>>(gdA, dA, didx, n2, g);
       if (need_c) scatter_kernel<<<nb, 256, 0, st>>>(gC, C, didx, n2, g);
@@ -350,5 +394,13 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
                                      const double* G_S, double* dA, double* C, double* S, int32_t force_m,
                                      int32_t force_s, cs_info* infos_host, cossin_stream_t stream) {
   return cs::backward_impl(count, n, 1.0, A, G_C, G_S, dA, C, S, force_m, force_s, infos_host,
-                           (cudaStream_t)stream);
+                           (cudaStream_t)stream, false);
+}
+
+extern "C" cs_status cossin_backward_ex(int64_t count, int64_t n, const double* A, const double* G_C,
+                                        const double* G_S, double* dA, double* C, double* S, int32_t force_m,
+                                        int32_t force_s, cs_prec prec, cs_info* infos_host, cossin_stream_t stream) {
+  if (prec != CS_FP64 && prec != CS_FP64_EMU) return cs::fail(CS_EINVAL, "the adjoint runs in CS_FP64 or CS_FP64_EMU");
+  return cs::backward_impl(count, n, 1.0, A, G_C, G_S, dA, C, S, force_m, force_s, infos_host,
+                           (cudaStream_t)stream, prec == CS_FP64_EMU);
 }

@@ -173,10 +173,14 @@ __device__ __forceinline__ void cut(double x, int e, __nv_bfloat16 (&q)[S]) {
 // Row maxima of |X| (rows x cols, leading dimension ld) without the entry
 // X[r][r mod cols], which goes to xd[r]: one warp per row.
 __global__ void __launch_bounds__(256) row_exp_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
-                                                      int64_t ld, int* __restrict__ ex, double* __restrict__ xd) {
+                                                      int64_t ld, int* __restrict__ ex, double* __restrict__ xd,
+                                                      int64_t bsx, int64_t rows_pad) {
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
+  X += (int64_t)blockIdx.y * bsx;  // matrix blockIdx.y of a batch
+  ex += (int64_t)blockIdx.y * rows_pad;
+  xd += (int64_t)blockIdx.y * rows_pad;
   const int64_t d = row % cols;
   double mx = 0.0;
   for (int64_t c = lane; c < cols; c += 32)
@@ -193,9 +197,12 @@ __global__ void __launch_bounds__(256) row_exp_kernel(const double* __restrict__
 // like their bits): atomicMax into colmax[cols], which starts at zero.
 // (Y is square here: the entry Y[c][c] is left out and goes to yd[c].)
 __global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__ Y, int64_t rows, int64_t cols,
-                                                      int64_t ld, unsigned long long* __restrict__ colmax) {
+                                                      int64_t ld, unsigned long long* __restrict__ colmax,
+                                                      int64_t bsy, int64_t cols_pad) {
   const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (c >= cols) return;
+  Y += (int64_t)blockIdx.z * bsy;
+  colmax += (int64_t)blockIdx.z * cols_pad;
   const int64_t r0 = (int64_t)blockIdx.y * 256;
   const int64_t r1 = std::min<int64_t>(rows, r0 + 256);
   double mx = 0.0;
@@ -205,23 +212,31 @@ __global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__
 }
 
 __global__ void col_exp_kernel(const double* __restrict__ Y, int64_t ld, const unsigned long long* __restrict__ colmax,
-                               int64_t cols, int* __restrict__ ex, double* __restrict__ yd) {
+                               int64_t cols, int* __restrict__ ex, double* __restrict__ yd, int64_t bsy,
+                               int64_t cols_pad) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Y += (int64_t)blockIdx.y * bsy;
+  colmax += (int64_t)blockIdx.y * cols_pad;
+  ex += (int64_t)blockIdx.y * cols_pad;
+  yd += (int64_t)blockIdx.y * cols_pad;
   if (c < cols) {
     ex[c] = line_exponent(__longlong_as_double((long long)colmax[c]));
     yd[c] = Y[c * ld + c];
   }
 }
 
-// Left operand: out[s][r][k] (row-major, K contiguous) for r < rows_pad,
-// k < ldk; rows >= rows and k >= cols are zero.
+// Left operand: out[b][s][r][k] (row-major, K contiguous) for r < rows_pad,
+// k < ldk, matrix b = blockIdx.y of a batch; rows >= rows and k >= cols are
+// zero.
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
                                                          int64_t ld, const int* __restrict__ ex,
                                                          __nv_bfloat16* __restrict__ out, int64_t rows_pad,
-                                                         int64_t ldk) {
-  const int64_t total = rows_pad * ldk;
+                                                         int64_t ldk, int64_t bsx) {
   const int64_t plane = rows_pad * ldk;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+  X += (int64_t)blockIdx.y * bsx;
+  ex += (int64_t)blockIdx.y * rows_pad;
+  out += (int64_t)blockIdx.y * S * plane;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / ldk, k = i - r * ldk;
     __nv_bfloat16 q[S];
     const double x = (r < rows && k < cols && k != r % cols) ? X[r * ld + k] : 0.0;
@@ -237,8 +252,11 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int64_t cols,
                                                          int64_t ld, const int* __restrict__ ex,
                                                          __nv_bfloat16* __restrict__ out, int64_t cols_pad,
-                                                         int64_t ldk) {
+                                                         int64_t ldk, int64_t bsy) {
   __shared__ __nv_bfloat16 tile[S][32][34];
+  Y += (int64_t)blockIdx.z * bsy;
+  ex += (int64_t)blockIdx.z * cols_pad;
+  out += (int64_t)blockIdx.z * S * cols_pad * ldk;
   const int64_t k0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int j = ty; j < 32; j += 8) {
@@ -270,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  int Mpad, int Npad, const int* __restrict__ ex, const int* __restrict__ fx,
                  const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y, int64_t ldy,
                  const double* __restrict__ xd, const double* __restrict__ yd, int64_t ldo,
-                 const __grid_constant__ Epilogue<double> epi, int* err) {
+                 const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kStages];
@@ -288,6 +306,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   // slices of all of B exceed L2 at n = 4096).
   const int nM = Mpad / BM, nN = Npad / BN;
   const int t = blockIdx.x;
+  // matrix blockIdx.y of a batch: its slices, exponents, operands and outputs
+  const int bat = blockIdx.y;
+  ex += (int64_t)bat * Mpad;
+  xd += (int64_t)bat * Mpad;
+  fx += (int64_t)bat * Npad;
+  yd += (int64_t)bat * Npad;
+  X += (int64_t)bat * bsx;
+  Y += (int64_t)bat * bsy;
+  const int64_t eoff = (int64_t)bat * bse;
   const int group = t / (kGroupM * nN);
   const int rows = min(kGroupM, nM - group * kGroupM);
   const int within = t - group * kGroupM * nN;
@@ -327,8 +354,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* base = smem + st * kStageBytes;
         mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
         for (int s = 0; s < S; ++s) {
-          tma_load_2d(base + s * kABytes, &mA, &full_bar[st], kb * BK, s * Mpad + m0);
-          tma_load_2d(base + S * kABytes + s * kBBytes, &mB, &full_bar[st], kb * BK, s * Npad + n0);
+          tma_load_2d(base + s * kABytes, &mA, &full_bar[st], kb * BK, (bat * S + s) * Mpad + m0);
+          tma_load_2d(base + S * kABytes + s * kBBytes, &mB, &full_bar[st], kb * BK, (bat * S + s) * Npad + n0);
         }
         kb_issued = kb + 1;
       }
@@ -474,9 +501,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool top = r < epi.split_row;
             const int64_t rr = top ? r : r - epi.split_row;
             const int t = top ? 0 : 1;
-            epi.out[t][rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
+            epi.out[t][eoff + rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
           } else {
-            const int64_t idx = (int64_t)r * ldo + cc;
+            const int64_t idx = eoff + (int64_t)r * ldo + cc;
             double in[EPI_MAX_IN], o[EPI_MAX_OUT];
 #pragma unroll
             for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
@@ -569,34 +596,37 @@ int grid_for(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256,
 
 }  // namespace
 
-OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K) {
+OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch) {
   OzakiDims d;
   d.Mpad = (M + BM - 1) / BM * BM;
   d.Npad = (N + BN - 1) / BN * BN;
   d.ldk = (K + 31) / 32 * 32;  // the slicing kernels work in 32 x 32 tiles
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  d.a_bytes = al((size_t)S * d.Mpad * d.ldk * 2);
-  d.b_bytes = al((size_t)S * d.Npad * d.ldk * 2);
-  d.ex_bytes = al(sizeof(int) * (size_t)d.Mpad);
-  d.fx_bytes = al(sizeof(int) * (size_t)d.Npad);
-  d.colmax_bytes = al(sizeof(unsigned long long) * (size_t)d.Npad);
-  d.xd_bytes = al(sizeof(double) * (size_t)d.Mpad);
-  d.yd_bytes = al(sizeof(double) * (size_t)d.Npad);
+  const size_t nb = (size_t)(batch > 0 ? batch : 1);
+  d.a_bytes = al(nb * S * d.Mpad * d.ldk * 2);
+  d.b_bytes = al(nb * S * d.Npad * d.ldk * 2);
+  d.ex_bytes = al(nb * sizeof(int) * (size_t)d.Mpad);
+  d.fx_bytes = al(nb * sizeof(int) * (size_t)d.Npad);
+  d.colmax_bytes = al(nb * sizeof(unsigned long long) * (size_t)d.Npad);
+  d.xd_bytes = al(nb * sizeof(double) * (size_t)d.Mpad);
+  d.yd_bytes = al(nb * sizeof(double) * (size_t)d.Npad);
   d.total = d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes + d.colmax_bytes + d.xd_bytes + d.yd_bytes;
   return d;
 }
 
-cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
-                       const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
-                       cudaStream_t stream) {
-  if (M <= 0 || N <= 0) return CS_OK;
+cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx,
+                               int64_t ldy, const Epilogue<double>& epi, int64_t ldo, int64_t batch, int64_t bsx,
+                               int64_t bsy, int64_t bse, void* work, size_t work_bytes, int* err,
+                               cudaStream_t stream) {
+  if (M <= 0 || N <= 0 || batch <= 0) return CS_OK;
   if (M > (1 << 20) || N > (1 << 20) || K > (1 << 20)) return fail(CS_EINVAL, "gemm_f64_emu: size too large");
   if (K <= 0 || N != K) return fail(CS_EINVAL, "gemm_f64_emu: the right operand must be square");
   if (K > kOzakiMaxK) return fail(CS_EINVAL, "gemm_f64_emu: K above 8192 (the int64 sums would overflow)");
-  const OzakiDims d = ozaki_dims(M, N, K);
+  if (batch > 65535) return fail(CS_EINVAL, "gemm_f64_emu: batch above 65535");
+  const OzakiDims d = ozaki_dims(M, N, K, batch);
   if (!work || work_bytes < d.total || ((uintptr_t)work & 255)) return fail(CS_EINVAL, "gemm_f64_emu: workspace");
   if (!err) return fail(CS_ECUDA, "gemm_f64_emu: no device error word");
-  if ((int64_t)S * d.Mpad > INT32_MAX || (int64_t)S * d.Npad > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: too large");
+  if (batch * S * d.Mpad > INT32_MAX || batch * S * d.Npad > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: too large");
   char* w = (char*)work;
   __nv_bfloat16* a_sl = (__nv_bfloat16*)w;
   __nv_bfloat16* b_sl = (__nv_bfloat16*)(w + d.a_bytes);
@@ -605,22 +635,24 @@ cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, i
   unsigned long long* colmax = (unsigned long long*)(w + d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes);
   double* xd = (double*)((char*)colmax + d.colmax_bytes);
   double* yd = (double*)((char*)xd + d.xd_bytes);
+  const unsigned nb = (unsigned)batch;
   {
-    ProfScope prof(CS_KERNEL_OTHER, (double)(M * K + K * N) * (8.0 + 2.0 * S), stream);
-    row_exp_kernel<<<(unsigned)((M + 7) / 8), 256, 0, stream>>>(X, M, K, ldx, ex, xd);
-    CS_CUDA_CHECK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)N, stream));
-    col_max_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)((K + 255) / 256)), 256, 0, stream>>>(Y, K, N, ldy,
-                                                                                                      colmax);
-    col_exp_kernel<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(Y, ldy, colmax, N, fx, yd);
-    slice_rows_kernel<<<grid_for(d.Mpad * d.ldk), 256, 0, stream>>>(X, M, K, ldx, ex, a_sl, d.Mpad, d.ldk);
-    slice_cols_kernel<<<dim3((unsigned)(d.Npad / 32), (unsigned)(d.ldk / 32)), 256, 0, stream>>>(Y, K, N, ldy, fx,
-                                                                                                 b_sl, d.Npad, d.ldk);
+    ProfScope prof(CS_KERNEL_OTHER, (double)batch * (double)(M * K + K * N) * (8.0 + 2.0 * S), stream);
+    row_exp_kernel<<<dim3((unsigned)((M + 7) / 8), nb), 256, 0, stream>>>(X, M, K, ldx, ex, xd, bsx, d.Mpad);
+    CS_CUDA_CHECK(cudaMemsetAsync(colmax, 0, d.colmax_bytes, stream));
+    col_max_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)((K + 255) / 256), nb), 256, 0, stream>>>(
+        Y, K, N, ldy, colmax, bsy, d.Npad);
+    col_exp_kernel<<<dim3((unsigned)((N + 255) / 256), nb), 256, 0, stream>>>(Y, ldy, colmax, N, fx, yd, bsy, d.Npad);
+    const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(d.Mpad * d.ldk), 152 * 16 / batch + 1));
+    slice_rows_kernel<<<dim3(sgrid, nb), 256, 0, stream>>>(X, M, K, ldx, ex, a_sl, d.Mpad, d.ldk, bsx);
+    slice_cols_kernel<<<dim3((unsigned)(d.Npad / 32), (unsigned)(d.ldk / 32), nb), 256, 0, stream>>>(
+        Y, K, N, ldy, fx, b_sl, d.Npad, d.ldk, bsy);
     CS_CUDA_CHECK(cudaGetLastError());
   }
-  ProfScope prof(CS_KERNEL_GEMM_EMU, 2.0 * (double)M * (double)N * (double)K, stream);
+  ProfScope prof(CS_KERNEL_GEMM_EMU, 2.0 * (double)batch * (double)M * (double)N * (double)K, stream);
   CUtensorMap mA, mB;
-  CS_CHECK(make_map(&mA, a_sl, (int64_t)S * d.Mpad, d.ldk, d.ldk, BM));
-  CS_CHECK(make_map(&mB, b_sl, (int64_t)S * d.Npad, d.ldk, d.ldk, BN));
+  CS_CHECK(make_map(&mA, a_sl, batch * S * d.Mpad, d.ldk, d.ldk, BM));
+  CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, BN));
   static bool attr_set = false;
   if (!attr_set) {
     CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
@@ -628,9 +660,42 @@ cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, i
   }
   const int64_t tiles = (d.Npad / BN) * (d.Mpad / BM);
   if (tiles > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: grid too large");
-  dim3 grid((unsigned)tiles);
+  dim3 grid((unsigned)tiles, nb);
   ozaki_kernel<<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex, fx,
-                                                  X, ldx, Y, ldy, xd, yd, ldo, epi, err);
+                                                  X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
+cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
+                       const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
+                       cudaStream_t stream) {
+  return gemm_f64_emu_batched(X, Y, M, N, K, ldx, ldy, epi, ldo, 1, 0, 0, 0, work, work_bytes, err, stream);
+}
+
+namespace {
+__global__ void __launch_bounds__(256) transpose_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                                        int64_t n, int64_t bs) {
+  __shared__ double tile[32][33];
+  src += (int64_t)blockIdx.z * bs;
+  dst += (int64_t)blockIdx.z * bs;
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < 32; j += 8)
+    if (r0 + j < n && c0 + tx < n) tile[j][tx] = src[(r0 + j) * n + c0 + tx];
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8)
+    if (c0 + j < n && r0 + tx < n) dst[(c0 + j) * n + r0 + tx] = tile[tx][j];
+}
+}  // namespace
+
+cs_status transpose_f64_batched(const double* src, double* dst, int64_t n, int64_t batch, int64_t bs,
+                                cudaStream_t stream) {
+  if (n <= 0 || batch <= 0) return CS_OK;
+  if (batch > 65535) return fail(CS_EINVAL, "transpose: batch above 65535");
+  ProfScope prof(CS_KERNEL_OTHER, 16.0 * (double)batch * (double)n * (double)n, stream);
+  const unsigned g = (unsigned)((n + 31) / 32);
+  transpose_kernel<<<dim3(g, g, (unsigned)batch), 256, 0, stream>>>(src, dst, n, bs);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }

@@ -118,7 +118,7 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
                       int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream, double scale);
 cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A, const double* G_C,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
-                        cs_info* infos_host, cudaStream_t stream);
+                        cs_info* infos_host, cudaStream_t stream, bool emu = false);
 cs_status check_prec(cs_prec prec);
 bool uses_emu(cs_prec p);  // CS_FP64_EMU, CS_SPLIT_EMU: FP64 products emulated on the tensor cores
 size_t elem_size(cs_prec p);

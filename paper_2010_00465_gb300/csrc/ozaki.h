@@ -24,7 +24,7 @@ struct OzakiDims {
   size_t a_bytes = 0, b_bytes = 0, ex_bytes = 0, fx_bytes = 0, colmax_bytes = 0, xd_bytes = 0, yd_bytes = 0;
   size_t total = 0;
 };
-OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K);
+OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch = 1);
 
 // P = X Y (X: M x K, Y: K x K, row-major FP64; M = K or the stacked 2K) with
 // the fused FP64 epilogue of gemm_f64 (stacked mode included); the entries
@@ -34,5 +34,18 @@ OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K);
 cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
                        const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
                        cudaStream_t stream);
+
+// The same over `batch` independent products: operand b at X + b bsx and
+// Y + b bsy, every epilogue matrix at + b bse; `work` holds
+// ozaki_dims(M, N, K, batch).total bytes.
+cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx,
+                               int64_t ldy, const Epilogue<double>& epi, int64_t ldo, int64_t batch, int64_t bsx,
+                               int64_t bsy, int64_t bse, void* work, size_t work_bytes, int* err,
+                               cudaStream_t stream);
+
+// dst_b = src_b^T for `batch` n x n row-major FP64 matrices at stride bs (dst
+// must not overlap src).
+cs_status transpose_f64_batched(const double* src, double* dst, int64_t n, int64_t batch, int64_t bs,
+                                cudaStream_t stream);
 
 }  // namespace cs

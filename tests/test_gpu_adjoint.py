@@ -136,3 +136,38 @@ def test_control_workload_sampled():
     Cm, Sm = api.cossin(cuda(A[b] - h * E), "fp64", m=m, s=s)
     fd = (np.sum(GC[b] * (Cp - Cm).cpu().numpy()) + np.sum(GS[b] * (Sp - Sm).cpu().numpy())) / (2 * h)
     assert abs(fd - float(np.sum(dA[b] * E))) <= 1e-7 * abs(fd)
+
+
+@pytest.mark.parametrize("n", [1, 17, 64, 130])
+@pytest.mark.parametrize("family,nrm", [("normal", 1.0), ("symmetric", 20.0), ("triangular", 3.0)])
+def test_emulated_products_match_oracle_gradient(n, family, nrm):
+    """The adjoint with its FP64 products emulated on the BF16 tensor cores
+    (batched, transposed operands materialised) against the oracle's
+    block-Frechet gradient."""
+    A = inputs.matrix(n, family, nrm, index=120, sub=n)
+    GC = inputs.matrix(n, "normal", None, index=121, sub=n)
+    GS = inputs.matrix(n, "normal", None, index=122, sub=n)
+    (dA, C, S), infos = api.cossin_backward(cuda(A), cuda(GC), cuda(GS), want_forward=True, return_info=True,
+                                            prec="fp64_emu")
+    m, s = infos[0]["m"], infos[0]["s"]
+    ref = oracle.gradient(A, GC, GS, m, s)
+    assert relfro(dA.cpu().numpy(), ref) <= TOL64
+    Co, So, _ = oracle.cossin(A, m=m, s=s)
+    assert relfro(C.cpu().numpy(), Co) <= TOL64 and relfro(S.cpu().numpy(), So) <= TOL64
+
+
+def test_emulated_control_workload_sampled():
+    A, GC, GS = inputs.hamiltonian_batch(512, 128)
+    dA = api.cossin_backward(cuda(A), cuda(GC), cuda(GS), prec="fp64_emu").cpu().numpy()
+    dA64 = api.cossin_backward(cuda(A), cuda(GC), cuda(GS)).cpu().numpy()
+    assert relfro(dA, dA64) <= 1e-12
+    for b in (3, 400):
+        m, s = oracle.select(oracle.norm1(A[b]), "double")
+        assert relfro(dA[b], oracle.gradient(A[b], GC[b], GS[b], m, s)) <= TOL64
+
+
+def test_emulated_adjoint_argument_errors():
+    A = torch.zeros(3, 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.CossinError) as ex:
+        api.cossin_backward(A, A, A, prec="fp32")
+    assert ex.value.status == _lib.CS_EINVAL
