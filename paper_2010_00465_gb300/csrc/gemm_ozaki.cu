@@ -95,11 +95,12 @@ constexpr int kBBytes = BN * BK * 2;   // one B slice of a stage
 constexpr int kStageBytes = S * (kABytes + kBBytes);
 constexpr int kStages = BK == 16 ? 4 : 2;
 constexpr int kGroupM = 8;             // M tiles per raster group
-constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kSmem = kStages * kStageBytes + 32 * (2 * (BN / 2) + 1) * 8 + 1024;  // stages + epilogue staging
 constexpr uint32_t kTmemCols = 512;
 static_assert(kAcc * BN <= (int)kTmemCols, "TMEM columns");
 static_assert(kSmem <= 227 * 1024, "shared memory");
-static_assert(BM * (BN + 1) * 8 <= kStages * S * (BM * BK * 2 + BN * BK * 2), "epilogue tile fits the stages");
+constexpr int kStageRows = 32;          // rows of the tile staged per epilogue round
+constexpr int kLd = 2 * kCols + 1;      // staging row pitch (doubles)
 // Instruction descriptors, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 // An N = 2 BN instruction reads the B slices q and q + 1, which lie next to
@@ -283,44 +284,48 @@ __device__ __forceinline__ double pow2(int e) {
   return ldexp(1.0, e);
 }
 
+// Persistent: CTA i takes the tiles i, i + gridDim.x, ... of the batch's
+// (matrix, tile) list.  Pipeline stages and chunks are counted across tiles,
+// so the producer and the MMA warp run on into the next tile while the
+// epilogue warps finish the previous one (its accumulators are released
+// before the FP64 epilogue, which stages through its own shared memory).
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int M, int N, int K,
-                 int Mpad, int Npad, const int* __restrict__ ex, const int* __restrict__ fx,
-                 const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y, int64_t ldy,
-                 const double* __restrict__ xd, const double* __restrict__ yd, int64_t ldo,
-                 const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse) {
+                 int Mpad, int Npad, const int* __restrict__ ex_all, const int* __restrict__ fx_all,
+                 const double* __restrict__ X_all, int64_t ldx, const double* __restrict__ Y_all, int64_t ldy,
+                 const double* __restrict__ xd_all, const double* __restrict__ yd_all, int64_t ldo,
+                 const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse,
+                 int batch) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  double* stage_tile = (double*)(smem + kStages * kStageBytes);  // kStageRows x kLd doubles
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
   __shared__ __align__(8) uint64_t chunk_bar;
   __shared__ __align__(8) uint64_t free_bar[kAcc];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ int stop_epi;
   __shared__ int kb_consumed;
   __shared__ int chunks_committed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Tiles in groups of kGroupM rows of M tiles, N fastest within a group, so
-  // that the CTAs resident at once share their slices of A and B in L2 (the
-  // slices of all of B exceed L2 at n = 4096).
   const int nM = Mpad / BM, nN = Npad / BN;
-  const int t = blockIdx.x;
-  // matrix blockIdx.y of a batch: its slices, exponents, operands and outputs
-  const int bat = blockIdx.y;
-  ex += (int64_t)bat * Mpad;
-  xd += (int64_t)bat * Mpad;
-  fx += (int64_t)bat * Npad;
-  yd += (int64_t)bat * Npad;
-  X += (int64_t)bat * bsx;
-  Y += (int64_t)bat * bsy;
-  const int64_t eoff = (int64_t)bat * bse;
-  const int group = t / (kGroupM * nN);
-  const int rows = min(kGroupM, nM - group * kGroupM);
-  const int within = t - group * kGroupM * nN;
-  const int m0 = (group * kGroupM + within % rows) * BM, n0 = (within / rows) * BN;
+  const int tiles_per_matrix = nM * nN;
+  const int total = tiles_per_matrix * batch;
   const int num_kb = (K + BK - 1) / BK;
   const int num_chunks = (num_kb + kChunkKb - 1) / kChunkKb;
+  // Tile t of a matrix: groups of kGroupM rows of M tiles, N fastest within a
+  // group, so that the CTAs resident at once share their slices in L2.
+  auto tile_of = [&](int u, int& bat, int& m0, int& n0) {
+    bat = u / tiles_per_matrix;
+    const int t = u - bat * tiles_per_matrix;
+    const int group = t / (kGroupM * nN);
+    const int rows = min(kGroupM, nM - group * kGroupM);
+    const int within = t - group * kGroupM * nN;
+    m0 = (group * kGroupM + within % rows) * BM;
+    n0 = (within / rows) * BN;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -330,6 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&chunk_bar, 1);
     for (int a = 0; a < kAcc; ++a) mbar_init(&free_bar[a], kEpiWarps);
     abort_flag = 0;
+    stop_epi = 0;
     kb_consumed = 0;
     chunks_committed = 0;
     fence_mbar_init();
@@ -345,188 +351,217 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       tma_prefetch(&mA);
       tma_prefetch(&mB);
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int st = kb % kStages;
-        if (kb >= kStages && !mbar_wait(&empty_bar[st], ((kb / kStages) & 1) ^ 1, &abort_flag)) {
-          abort_flag = 1;
-          break;
+      int g = 0;  // k-blocks issued so far, over all tiles
+      for (int u = blockIdx.x; u < total && !abort_flag; u += gridDim.x) {
+        int bat, m0, n0;
+        tile_of(u, bat, m0, n0);
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          const int st = g % kStages;
+          if (g >= kStages && !mbar_wait(&empty_bar[st], ((g / kStages) & 1) ^ 1, &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          uint8_t* base = smem + st * kStageBytes;
+          mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+          for (int s = 0; s < S; ++s) {
+            tma_load_2d(base + s * kABytes, &mA, &full_bar[st], kb * BK, (bat * S + s) * Mpad + m0);
+            tma_load_2d(base + S * kABytes + s * kBBytes, &mB, &full_bar[st], kb * BK, (bat * S + s) * Npad + n0);
+          }
+          kb_issued = g + 1;
         }
-        uint8_t* base = smem + st * kStageBytes;
-        mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
-        for (int s = 0; s < S; ++s) {
-          tma_load_2d(base + s * kABytes, &mA, &full_bar[st], kb * BK, (bat * S + s) * Mpad + m0);
-          tma_load_2d(base + S * kABytes + s * kBBytes, &mB, &full_bar[st], kb * BK, (bat * S + s) * Npad + n0);
-        }
-        kb_issued = kb + 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // Descriptor words: the low word carries the start address (>> 4) and
-      // LBO = 1, the high word SBO = 512 B, version 1 and the 64-byte
-      // swizzle; every operand of a stage is at a compile-time offset from
-      // the stage base, so each MMA costs two integer adds to issue.
-      // SBO = 8 rows x swizzle bytes; layout type 6 = 32-byte, 4 = 64-byte swizzle
+      // LBO = 1, the high word SBO = 8 rows x swizzle bytes, version 1 and
+      // the swizzle mode (6 = 32-byte, 4 = 64-byte); every operand of a stage
+      // is at a compile-time offset from the stage base, so each MMA costs
+      // two integer adds to issue.
       constexpr uint32_t kDescHi =
           ((uint32_t)(8 * kSwizzleBytes) >> 4) | (1u << 14) | ((kSwizzleBytes == 32 ? 6u : 4u) << 29);
-      int kb = 0;
-      for (int c = 0; c < num_chunks && !abort_flag; ++c) {
-        for (int kk = 0; kk < kChunkKb && kb < num_kb; ++kk, ++kb) {
-          const int st = kb % kStages;
-          if (!mbar_wait(&full_bar[st], (kb / kStages) & 1, &abort_flag)) {
-            abort_flag = 1;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a_lo = ((smem_u32(smem + st * kStageBytes) & 0x3FFFFu) >> 4) | (1u << 16);
-          const uint32_t b_lo = a_lo + (uint32_t)((S * kABytes) >> 4);
-          const bool chunk_start = kk == 0;
-          const bool wait_free = kk == 0 && c > 0;
-          bool stop = false;
+      int g = 0;   // k-blocks consumed so far, over all tiles
+      int cg = 0;  // chunks committed so far, over all tiles
+      for (int u = blockIdx.x; u < total && !abort_flag; u += gridDim.x) {
+        int kb = 0;
+        for (int c = 0; c < num_chunks && !abort_flag; ++c, ++cg) {
+          for (int kk = 0; kk < kChunkKb && kb < num_kb; ++kk, ++kb, ++g) {
+            const int st = g % kStages;
+            if (!mbar_wait(&full_bar[st], (g / kStages) & 1, &abort_flag)) {
+              abort_flag = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_lo = ((smem_u32(smem + st * kStageBytes) & 0x3FFFFu) >> 4) | (1u << 16);
+            const uint32_t b_lo = a_lo + (uint32_t)((S * kABytes) >> 4);
+            const bool chunk_start = kk == 0;
+            const bool wait_free = kk == 0 && cg > 0;
+            bool stop = false;
 #pragma unroll
-          for (int j = 0; j < BK / 16 && !stop; ++j) {  // K = 16 bf16 (32 bytes) per instruction
+            for (int j = 0; j < BK / 16 && !stop; ++j) {  // K = 16 bf16 (32 bytes) per instruction
 #pragma unroll
-            for (int p = 0; p < S; ++p) {
-              const uint64_t ad = ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
-              // pairs (p, q), (p, q + 1) for q = 0, 2, ...: levels p + q, p + q + 1 < S
+              for (int p = 0; p < S; ++p) {
+                const uint64_t ad =
+                    ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
+                // pairs (p, q), (p, q + 1) for q = 0, 2, ...: levels p + q, p + q + 1 < S
 #pragma unroll
-              for (int q = 0; p + q + 1 < S; q += 2) {
-                const uint64_t bd =
-                    ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
-                // p = 0 touches every level first: there a chunk restarts its
-                // accumulators, after the epilogue has read them
-                const bool restart = chunk_start && j == 0 && p == 0;
-                if (restart && wait_free) {
-                  if (!mbar_wait(&free_bar[q], (c - 1) & 1, &abort_flag) ||
-                      !mbar_wait(&free_bar[q + 1], (c - 1) & 1, &abort_flag)) {
-                    abort_flag = 1;
-                    stop = true;
-                    break;
+                for (int q = 0; p + q + 1 < S; q += 2) {
+                  const uint64_t bd =
+                      ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
+                  // p = 0 touches every level first: there a chunk restarts
+                  // its accumulators, after the epilogue has read them
+                  const bool restart = chunk_start && j == 0 && p == 0;
+                  if (restart && wait_free) {
+                    if (!mbar_wait(&free_bar[q], (cg - 1) & 1, &abort_flag) ||
+                        !mbar_wait(&free_bar[q + 1], (cg - 1) & 1, &abort_flag)) {
+                      abort_flag = 1;
+                      stop = true;
+                      break;
+                    }
+                    tc_fence_after();
                   }
-                  tc_fence_after();
+                  mma_bf16(tmem + (uint32_t)((p + q) * BN), ad, bd, kIdesc2, restart ? 0u : 1u);
                 }
-                mma_bf16(tmem + (uint32_t)((p + q) * BN), ad, bd, kIdesc2, restart ? 0u : 1u);
-              }
-              if (stop) break;
-              if ((S - p) & 1) {  // the last pair (p, S - 1 - p) alone, level S - 1
-                const int q = S - 1 - p;
-                const uint64_t bd =
-                    ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
-                mma_bf16(tmem + (uint32_t)((S - 1) * BN), ad, bd, kIdesc1, 1u);
+                if (stop) break;
+                if ((S - p) & 1) {  // the last pair (p, S - 1 - p) alone, level S - 1
+                  const int q = S - 1 - p;
+                  const uint64_t bd =
+                      ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
+                  mma_bf16(tmem + (uint32_t)((S - 1) * BN), ad, bd, kIdesc1, 1u);
+                }
               }
             }
+            if (stop) break;
+            mma_commit(&empty_bar[st]);
+            kb_consumed = g + 1;
           }
-          if (stop) break;
-          mma_commit(&empty_bar[st]);
-          kb_consumed = kb + 1;
+          mma_commit(&chunk_bar);  // also tracks the MMAs of an aborted chunk
+          chunks_committed = cg + 1;
         }
-        mma_commit(&chunk_bar);  // also tracks the MMAs of an aborted chunk
-        chunks_committed = c + 1;
       }
     }
   } else {
     const int quarter = warp & 3;                // TMEM lanes 32*quarter .. +31
     const int col0 = ((warp - 2) >> 2) * kCols;  // this warp's 32 columns
+    const int we = warp - 2;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    // Fixed-point sums with quantum 2^-35 of the slice products: each
-    // chunk's level-L value (L <= 4) is an integer multiple of 2^(-7L) below
-    // 2^24 quanta and converts exactly; the levels above 4 are rounded to
-    // 2^-35.  For K <= 8192 the sum stays below 2^63.
-    long long acc[kCols];
+    int cg = 0;  // chunks drained so far, over all tiles
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+      int bat, m0, n0;
+      tile_of(u, bat, m0, n0);
+      // Fixed-point sums with quantum 2^-35 of the slice products: each
+      // chunk's level-L value (L <= 5) is an integer multiple of 2^(-7L) below
+      // 2^24 quanta and converts exactly; levels 6, 7 are rounded to 2^-35.
+      // For K <= 8192 the sum stays below 2^63.
+      long long acc[kCols];
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) acc[j] = 0;
-    bool ok = true;
-    for (int c = 0; c < num_chunks; ++c) {
-      int w = 1;
-      if (lane == 0) {
-        w = mbar_wait(&chunk_bar, c & 1, &abort_flag) && !abort_flag;
-        if (!w) abort_flag = 1;
-      }
-      w = __shfl_sync(0xffffffffu, w, 0);
-      if (!w) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-#pragma unroll 1
-      for (int a = 0; a < kAcc; ++a) {
-        uint32_t v0[16], v1[16];
-        const uint32_t t = tmem + lane_off + (uint32_t)(a * BN + col0);
-        tmem_ld16(t, v0);
-        tmem_ld16(t + 16u, v1);
-        tmem_ld_wait();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&free_bar[a]);
-        const int e = 7 * a < 35 ? 7 * a : 35;  // value * 2^e is an integer (rounded for levels > 5)
-        const float sc = __int_as_float((127 + e) << 23);
-        const long long unit = 1LL << (35 - e);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          acc[j] += (long long)__float2int_rn(__uint_as_float(v0[j]) * sc) * unit;
-          acc[16 + j] += (long long)__float2int_rn(__uint_as_float(v1[j]) * sc) * unit;
+      for (int j = 0; j < kCols; ++j) acc[j] = 0;
+      bool ok = true;
+      for (int c = 0; c < num_chunks; ++c, ++cg) {
+        int w = 1;
+        if (lane == 0) {
+          w = mbar_wait(&chunk_bar, cg & 1, &abort_flag) && !abort_flag;
+          if (!w) abort_flag = 1;
         }
-      }
-    }
-    // Stage the tile (FP64 sums, row stride 2 kCols + 1 doubles) in the
-    // shared memory of the finished pipeline, then walk it row by row.
-    double* tile = (double*)smem;
-    constexpr int kLd = 2 * kCols + 1;
-    if (ok) {
-      const int rl = quarter * 32 + lane;
-#pragma unroll
-      for (int j = 0; j < kCols; ++j) tile[rl * kLd + col0 + j] = (double)acc[j];
-    }
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
-    if (!abort_flag) {
-      const int we = warp - 2;
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (!w) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
 #pragma unroll 1
-      for (int rl = we; rl < BM; rl += kEpiWarps) {
-        const int r = m0 + rl;
-        if (r >= M) break;
-        const int er = ex[r] - 14 - 35;
-        const int d = r % K;
-        const double xdr = xd[r];
-        const double* __restrict__ yrow = Y + (int64_t)d * ldy;
-        const double* __restrict__ xrow = X + (int64_t)r * ldx;
+        for (int a = 0; a < kAcc; ++a) {
+          uint32_t v0[16], v1[16];
+          const uint32_t tq = tmem + lane_off + (uint32_t)(a * BN + col0);
+          tmem_ld16(tq, v0);
+          tmem_ld16(tq + 16u, v1);
+          tmem_ld_wait();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&free_bar[a]);
+          const int e = 7 * a < 35 ? 7 * a : 35;  // value * 2^e is an integer (rounded for levels > 5)
+          const float sc = __int_as_float((127 + e) << 23);
+          const long long unit = 1LL << (35 - e);
 #pragma unroll
-        for (int h = 0; h < BN / 32; ++h) {
-          const int cl = 32 * h + lane;
-          const int cc = n0 + cl;
-          if (cc >= N) continue;
-          // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
-          const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
-          const double p = fma(tile[rl * kLd + cl], pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
-          if (epi.split_row >= 0) {
-            const bool top = r < epi.split_row;
-            const int64_t rr = top ? r : r - epi.split_row;
-            const int t = top ? 0 : 1;
-            epi.out[t][eoff + rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
-          } else {
-            const int64_t idx = eoff + (int64_t)r * ldo + cc;
-            double in[EPI_MAX_IN], o[EPI_MAX_OUT];
-#pragma unroll
-            for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
-#pragma unroll
-            for (int t = 0; t < EPI_MAX_OUT; ++t) {
-              if (t >= epi.n_out) break;
-              double v = epi.alpha[t] * p + (r == cc ? epi.gamma[t] : 0.0);
-#pragma unroll
-              for (int q = 0; q < EPI_MAX_IN; ++q)
-                if (q < epi.n_in) v += epi.beta[t][q] * in[q];
-#pragma unroll
-              for (int u = 0; u < EPI_MAX_OUT; ++u)
-                if (u < t) v += epi.delta[t][u] * o[u];
-              o[t] = v;
-            }
-#pragma unroll
-            for (int t = 0; t < EPI_MAX_OUT; ++t) {
-              if (t >= epi.n_out) break;
-              epi.out[t][idx] = o[t];
-            }
+          for (int j = 0; j < 16; ++j) {
+            acc[j] += (long long)__float2int_rn(__uint_as_float(v0[j]) * sc) * unit;
+            acc[16 + j] += (long long)__float2int_rn(__uint_as_float(v1[j]) * sc) * unit;
           }
         }
       }
+      // FP64 epilogue, one quarter of the tile (32 rows) at a time: the two
+      // warps holding it stage their sums, then all eight walk its rows with
+      // coalesced loads and stores.
+      const int* __restrict__ ex = ex_all + (int64_t)bat * Mpad;
+      const int* __restrict__ fx = fx_all + (int64_t)bat * Npad;
+      const double* __restrict__ xd = xd_all + (int64_t)bat * Mpad;
+      const double* __restrict__ yd = yd_all + (int64_t)bat * Npad;
+      const double* __restrict__ X = X_all + (int64_t)bat * bsx;
+      const double* __restrict__ Y = Y_all + (int64_t)bat * bsy;
+      const int64_t eoff = (int64_t)bat * bse;
+#pragma unroll 1
+      for (int qr = 0; qr < 4; ++qr) {
+        if (quarter == qr && ok) {
+#pragma unroll
+          for (int j = 0; j < kCols; ++j) stage_tile[lane * kLd + col0 + j] = (double)acc[j];
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+        if (we == 0 && lane == 0) stop_epi = abort_flag;
+        if (!abort_flag) {
+#pragma unroll 1
+          for (int rq = we; rq < kStageRows; rq += kEpiWarps) {
+            const int rl = qr * kStageRows + rq;
+            const int r = m0 + rl;
+            if (r >= M) break;
+            const int er = ex[r] - 14 - 35;
+            const int d = r % K;
+            const double xdr = xd[r];
+            const double* __restrict__ yrow = Y + (int64_t)d * ldy;
+            const double* __restrict__ xrow = X + (int64_t)r * ldx;
+#pragma unroll
+            for (int h = 0; h < BN / 32; ++h) {
+              const int cl = 32 * h + lane;
+              const int cc = n0 + cl;
+              if (cc >= N) continue;
+              // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
+              const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
+              const double p = fma(stage_tile[rq * kLd + cl], pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
+              if (epi.split_row >= 0) {
+                const bool top = r < epi.split_row;
+                const int64_t rr = top ? r : r - epi.split_row;
+                const int t = top ? 0 : 1;
+                epi.out[t][eoff + rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
+              } else {
+                const int64_t idx = eoff + (int64_t)r * ldo + cc;
+                double in[EPI_MAX_IN], o[EPI_MAX_OUT];
+#pragma unroll
+                for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
+#pragma unroll
+                for (int t = 0; t < EPI_MAX_OUT; ++t) {
+                  if (t >= epi.n_out) break;
+                  double v = epi.alpha[t] * p + (r == cc ? epi.gamma[t] : 0.0);
+#pragma unroll
+                  for (int q = 0; q < EPI_MAX_IN; ++q)
+                    if (q < epi.n_in) v += epi.beta[t][q] * in[q];
+#pragma unroll
+                  for (int uu = 0; uu < EPI_MAX_OUT; ++uu)
+                    if (uu < t) v += epi.delta[t][uu] * o[uu];
+                  o[t] = v;
+                }
+#pragma unroll
+                for (int t = 0; t < EPI_MAX_OUT; ++t) {
+                  if (t >= epi.n_out) break;
+                  epi.out[t][idx] = o[t];
+                }
+              }
+            }
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+      }
+      // every epilogue warp reads the same stop flag (written before the
+      // last barrier), so all of them leave the tile loop together
+      if (stop_epi) break;
     }
   }
 
@@ -536,8 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (abort_flag) {
     if (warp == 0 && lane == 0) {
       volatile int never = 0;
-      for (int kb = kb_consumed; kb < kb_issued; ++kb)
-        mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1, &never);
+      for (int g = kb_consumed; g < kb_issued; ++g) mbar_wait(&full_bar[g % kStages], (g / kStages) & 1, &never);
     }
     if (warp == 1 && lane == 0 && chunks_committed > 0) {
       volatile int never = 0;
@@ -658,11 +692,14 @@ cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int6
     CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr_set = true;
   }
-  const int64_t tiles = (d.Npad / BN) * (d.Mpad / BM);
+  const int64_t tiles = (d.Npad / BN) * (d.Mpad / BM) * batch;
   if (tiles > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: grid too large");
-  dim3 grid((unsigned)tiles, nb);
+  int sms = 0, dev = 0;
+  CS_CUDA_CHECK(cudaGetDevice(&dev));
+  CS_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms > 0 ? sms : 1);
   ozaki_kernel<<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex, fx,
-                                                  X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse);
+                                                  X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse, (int)batch);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
