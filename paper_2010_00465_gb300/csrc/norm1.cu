@@ -23,7 +23,9 @@ constexpr int kRows = 64;   // rows per chunk in pass 1
 
 template <typename T>
 __global__ void __launch_bounds__(kCols) colsum_partial(const T* __restrict__ A, int64_t n,
-                                                        double* __restrict__ partial) {
+                                                        double* __restrict__ partial, unsigned int* __restrict__ ticket) {
+  // pass 2 counts its blocks on this word; pass 1 runs first on the stream
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ticket = 0u;
   const int64_t col = (int64_t)blockIdx.x * kCols + threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.y * kRows;
   if (col >= n) return;
@@ -56,9 +58,19 @@ __global__ void __launch_bounds__(kCols) colsum_finish(const double* __restrict_
   const int64_t col = (int64_t)blockIdx.x * kCols + threadIdx.x;
   double best = 0.0;
   if (col < n) {
-    double s = 0.0;
-    for (int64_t k = 0; k < chunks; ++k) s += partial[k * n + col];
-    best = s;
+    // four interleaved sums in a fixed order (deterministic), sixteen loads
+    // in flight per thread
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t k = 0;
+    for (; k + 16 <= chunks; k += 16) {
+      double v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = partial[(k + u) * n + col];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) s4[u & 3] += v[u];
+    }
+    for (; k < chunks; ++k) s4[k & 3] += partial[k * n + col];
+    best = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   }
   __shared__ double warp_best[kCols / 32];
   __shared__ bool last;
@@ -125,9 +137,8 @@ cs_status norm1_impl(const T* A, int64_t n, double* partial, double* out, cudaSt
   double* block_max = partial + chunks * n;
   unsigned int* ticket = (unsigned int*)(block_max + col_blocks);
   ProfScope prof(CS_KERNEL_NORM1, (double)n * (double)n * sizeof(T), stream);
-  CS_CUDA_CHECK(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), stream));
   dim3 grid((unsigned)col_blocks, (unsigned)chunks);
-  colsum_partial<T><<<grid, kCols, 0, stream>>>(A, n, partial);
+  colsum_partial<T><<<grid, kCols, 0, stream>>>(A, n, partial, ticket);
   colsum_finish<<<(unsigned)col_blocks, kCols, 0, stream>>>(partial, n, chunks, block_max, ticket, out);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
