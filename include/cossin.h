@@ -165,6 +165,12 @@ cs_status cossin_ex(const void* A_dev, int64_t n, cs_prec prec, void* C_dev, voi
  * CS_ENONFINITE if t^2 ||A||_1 is not finite, CS_ERANGE if sigma would
  * exceed 64, CS_EINVAL for a non-finite t or bad arguments.  ws_dev may be
  * NULL, in which case the workspace is allocated on `stream` as in cossin. */
+/* The choice cossin_cs makes, on the host: the family (0..3) and sigma of
+ * minimal products + 2 sigma with ||B||_1 / 4^sigma <= theta_cs (table 0:
+ * double, 1: single; ties go to the smaller sigma).  CS_ENONFINITE for a
+ * non-finite norm, CS_ERANGE beyond 64 steps, CS_EINVAL for a negative norm. */
+cs_status cossin_cs_select(double normB, int32_t table, int32_t* family, int32_t* sigma);
+
 cs_status cossin_cs(const void* A_dev, int64_t n, double t, cs_prec prec, void* C_dev, void* S_dev,
                     void* ws_dev, size_t ws_bytes, int32_t force_family, int32_t force_sigma,
                     cs_info* info, cossin_stream_t stream);

@@ -45,6 +45,7 @@ SIGNATURES = {
     "cossin": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp]),
     "cossin_ex": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp, _vp, _sz, _i32, _i32,
                                  ctypes.POINTER(CsInfo), _vp]),
+    "cossin_cs_select": (ctypes.c_int, [ctypes.c_double, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "cossin_cs": (ctypes.c_int, [_vp, _i64, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _sz, _i32, _i32,
                                  ctypes.POINTER(CsInfo), _vp]),
     "cossin_matmul": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),

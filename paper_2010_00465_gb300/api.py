@@ -106,6 +106,14 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
     return C, S
 
 
+def cs_select(normB: float, table: int):
+    """(family, sigma) that cossin_cs takes for ||t^2 A||_1 = normB; table 0 = double, 1 = single."""
+    f = ctypes.c_int32()
+    sg = ctypes.c_int32()
+    check(lib().cossin_cs_select(float(normB), int(table), ctypes.byref(f), ctypes.byref(sg)))
+    return f.value, sg.value
+
+
 def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None, sigma: int | None = None,
               workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
     """c(t^2 A) = cos(sqrt(t^2 A)) and s(t, A) = A^(-1/2) sin(sqrt(t^2 A)) (Sec. 2.2).

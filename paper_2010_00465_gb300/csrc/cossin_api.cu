@@ -669,6 +669,19 @@ cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, v
   return rc;
 }
 
+cs_status cossin_cs_select(double normB, int32_t table, int32_t* family, int32_t* sigma) {
+  if (table < 0 || table > 1) return cs::fail(CS_EINVAL, "cs_select: table must be 0 (double) or 1 (single)");
+  if (!family || !sigma) return cs::fail(CS_EINVAL, "cs_select: null output pointer");
+  if (normB < 0) return cs::fail(CS_EINVAL, "cs_select: negative norm");
+  int f = 0, sg = 0;
+  const int rc = cs::select_cs_family(normB, table, &f, &sg);
+  if (rc == 3) return cs::fail(CS_ENONFINITE, "cs_select: ||t^2 A||_1 is not finite");
+  if (rc == 4) return cs::fail(CS_ERANGE, "cs_select: more than 64 double-angle steps needed");
+  *family = f;
+  *sigma = sg;
+  return CS_OK;
+}
+
 const char* cossin_last_error(void) { return cs::g_last_error.c_str(); }
 
 cs_status cossin_device_status(cossin_stream_t stream) {

@@ -129,3 +129,18 @@ def test_cs_and_unitary_argument_errors_before_any_gpu_work(L):
     ub = L.cossin_unitary_backward
     assert ub(0, 4, 1.0, nul, nul, nul, nul, -1, -1, nul, nul) == _lib.CS_OK
     assert ub(1, 4, float("nan"), nul, nul, nul, nul, -1, -1, nul, nul) == _lib.CS_EINVAL
+
+
+@pytest.mark.parametrize("table,prec", [(0, "double"), (1, "single")])
+def test_cs_select_matches_oracle(L, table, prec):
+    """The library's c/s selection (its own theta_cs table) against the oracle's."""
+    for nrm in np.concatenate([[0.0], np.geomspace(1e-8, 1e30, 900)]):
+        assert api.cs_select(float(nrm), table) == oracle.cs_select(float(nrm), prec), nrm
+
+
+def test_cs_select_errors(L):
+    for bad, st in ((float("inf"), _lib.CS_ENONFINITE), (float("nan"), _lib.CS_ENONFINITE),
+                    (1e300, _lib.CS_ERANGE), (-1.0, _lib.CS_EINVAL)):
+        with pytest.raises(_lib.CossinError) as e:
+            api.cs_select(bad, 0)
+        assert e.value.status == st
