@@ -173,3 +173,27 @@ def test_brute_force_series(nrm):
     f = lambda X: np.array([[float(X[i, j]) for j in range(n)] for i in range(n)])
     C, S, _ = oracle.cs(A, t)
     assert relfro(C, f(Cs)) < 1e-13 and relfro(S, f(Ss)) < 1e-13
+
+
+def _horner(coef, B):
+    n = B.shape[0]
+    P = float(coef[-1]) * np.eye(n)
+    for c in reversed(coef[:-1]):
+        P = P @ B + float(c) * np.eye(n)
+    return P
+
+
+@pytest.mark.parametrize("family", [0, 1, 2, 3])
+def test_schemes_equal_expanded_polynomials(family):
+    """c and s of each family equal their expanded polynomials in B = t^2 A
+    (s times t) evaluated by Horner's rule, at sigma = 0 with ||B||_1 at and
+    below theta_cs, to rounding level."""
+    cb, sb = pp.cs_coefficients(family)
+    th = oracle.cs_theta("double", family)
+    for frac, idx in ((1.0, 0), (0.5, 1)):
+        A = inputs.matrix(18, "normal", 1.0, index=150 + idx, sub=family)
+        t = float(np.sqrt(frac * th / oracle.norm1(A)))
+        C, S, _ = oracle.cs(A, t, family=family, sigma=0)
+        B = t * t * A
+        assert relfro(C, _horner(cb, B)) < 1e-14
+        assert relfro(S, t * _horner(sb, B)) < 1e-14

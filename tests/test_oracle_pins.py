@@ -415,3 +415,32 @@ def test_gradient_adjoint_identity():
     gs = oracle.gradient(A, np.zeros_like(G), G, m, s)
     assert abs(np.sum(G * Lc) - np.sum(gc * E)) < 1e-11 * np.abs(G).sum() * np.abs(Lc).max()
     assert abs(np.sum(G * Ls) - np.sum(gs * E)) < 1e-11 * np.abs(G).sum() * np.abs(Ls).max()
+
+
+def _horner(coef, A):
+    """p(A) = sum_k coef[k] A^k by Horner's rule in FP64 (numpy products)."""
+    n = A.shape[0]
+    P = float(coef[-1]) * np.eye(n)
+    for c in reversed(coef[:-1]):
+        P = P @ A + float(c) * np.eye(n)
+    return P
+
+
+@pytest.mark.parametrize("m", [4, 8, 9, 16, 24])
+@pytest.mark.parametrize("family", ["normal", "symmetric", "triangular"])
+def test_chain_equals_expanded_polynomial(m, family):
+    """The factorised chain of each family equals its expanded polynomial
+    (coefficients from the high-precision expansion of the printed ones)
+    evaluated by Horner's rule, on random A at and below the family's
+    admissible norm (s = 0), to rounding level."""
+    ck, sk, _, _ = FAM[m]
+    polys = pp.schemes(refined=False)
+    mm = 8 if m == 9 else m
+    th = min(oracle.theta("double", mm, False), oracle.theta("double", mm, True))
+    for frac, idx in ((1.0, 0), (0.5, 1)):
+        A = inputs.matrix(20, family, frac * th, index=140 + idx, sub=m)
+        C, S, _ = oracle.cossin(A, "double", m=m, s=0)
+        Ch = _horner(polys[ck], A)
+        Sh = _horner(polys[sk], A)
+        assert relfro(C, Ch) < 1e-14, (m, family, frac, relfro(C, Ch))
+        assert relfro(S, Sh) < 1e-14, (m, family, frac, relfro(S, Sh))
