@@ -215,10 +215,19 @@ def main():
 
     infos = []
 
+    case_ms = []
+
     def step(record=False):
         for (p, f, r), A, (C, S) in zip(work, dev_in, outs):
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(torch.cuda.current_stream())
             _, _, info = api.cossin(A, p, workspace=wsp, out=(C, S), return_info=True)
             if record:
+                e1.record(torch.cuda.current_stream())
+                e1.synchronize()
+                case_ms.append(e0.elapsed_time(e1))
                 infos.append(info)
 
     for _ in range(max(args.warmup, 0)):
@@ -337,8 +346,10 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "accuracy": acc,
         "alt_fp64_emu": alt,
-        "per_case": [{"prec": p, "family": f, "norm1": r, "m": i["m"], "s": i["s"], "products": i["products"]}
-                     for (p, f, r), i in zip(work, infos)],
+        "per_case": [{"prec": p, "family": f, "norm1": r, "m": i["m"], "s": i["s"], "products": i["products"],
+                      "ms": t, "alg_tflops": i["flops"] / t / 1e9,
+                      "rel_diff_vs_fp64_path": acc.get("%s_vs_fp64_path_%s_norm%g" % (p, f, r), 0.0 if p == "fp64" else None)}
+                     for (p, f, r), i, t in zip(work, infos, case_ms)],
         "kernels": {k: {"ms": v[0], "launches": v[1], "work": v[2]} for k, v in kern.items()},
     }
     if rank == 0 and not args.no_forms:
@@ -647,7 +658,17 @@ def accuracy(api, dev_in, outs, work):
     res = {}
     A = inputs.matrix(64, "normal", 2.0, index=0)
     Co, So, _ = oracle.cossin(A)
-    C, S = api.cossin(torch.from_numpy(A).cuda(), "fp64")
+    Ad = torch.from_numpy(A).cuda()
+    C, S = api.cossin(Ad, "fp64")
+    # the 64 x 64 configuration's latency per call (norm, its one host
+    # synchronisation, 9 products), median of 50
+    ts = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        api.cossin(Ad, "fp64")
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    res["fp64_64x64_latency_us"] = float(np.median(ts) * 1e6)
     res["fp64_64x64_rel_err_vs_oracle"] = max(
         float(np.linalg.norm(C.cpu().numpy() - Co) / np.linalg.norm(Co)),
         float(np.linalg.norm(S.cpu().numpy() - So) / np.linalg.norm(So)))
