@@ -175,6 +175,15 @@ cs_status cossin_cs(const void* A_dev, int64_t n, double t, cs_prec prec, void* 
                     void* ws_dev, size_t ws_bytes, int32_t force_family, int32_t force_sigma,
                     cs_info* info, cossin_stream_t stream);
 
+/* Failure-path self test (the paper has no counterpart): launches one
+ * tensor-core-style bounded wait on an mbarrier that nothing arrives at, with
+ * a limit of about 1 ms.  The wait gives up and raises the device error word
+ * exactly as an expired wait in the tensor-core kernels would, so the next
+ * call that synchronises (cossin, cossin_ex, cossin_cs, ...) returns
+ * CS_ETIMEOUT and clears the word; the context stays usable.  Returns CS_OK
+ * once the kernel is queued on `stream`. */
+cs_status cossin_selftest_wait_timeout(cossin_stream_t stream);
+
 /* One product P = X Y (n x n, row-major) on the library's product kernel for
  * `prec`: the FP64 kernel for CS_FP64, the four-pass TF32 tensor-core kernel
  * for CS_FP32 (FP32 in and out) and CS_SPLIT_TF32 (FP64 in and out, computed

@@ -64,6 +64,7 @@ SIGNATURES = {
     "cossin_batched_plan_launch": (ctypes.c_int, [_vp, _vp]),
     "cossin_batched_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "cossin_batched_plan_destroy": (ctypes.c_int, [_vp]),
+    "cossin_selftest_wait_timeout": (ctypes.c_int, [_vp]),
     "cossin_last_error": (ctypes.c_char_p, []),
     "cossin_device_status": (ctypes.c_int, [_vp]),
     "cossin_prof_enable": (None, [_i32]),

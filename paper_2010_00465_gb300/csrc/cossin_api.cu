@@ -682,6 +682,11 @@ cs_status cossin_cs_select(double normB, int32_t table, int32_t* family, int32_t
   return CS_OK;
 }
 
+cs_status cossin_selftest_wait_timeout(cossin_stream_t stream) {
+  // about 1 ms at 2 GHz: the kernel gives up, raises the error word, returns
+  return cs::wait_selftest(2000000LL, (cudaStream_t)stream);
+}
+
 const char* cossin_last_error(void) { return cs::g_last_error.c_str(); }
 
 cs_status cossin_device_status(cossin_stream_t stream) {

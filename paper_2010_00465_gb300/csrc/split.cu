@@ -109,6 +109,29 @@ cs_status combine_f64(const float* hi, const float* lo, int64_t n, int64_t ld, d
   return combine_impl<double>(hi, lo, n, ld, dst, stream);
 }
 
+namespace {
+// The failure path of every bounded wait, exercised on purpose: an mbarrier
+// that nothing arrives at, waited on with a short limit; on expiry the kernel
+// raises the error word the tensor-core kernels raise and returns.
+__global__ void wait_selftest_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  ptx::mbar_init(&bar, 1);
+  ptx::fence_mbar_init();
+  if (!ptx::mbar_wait_limit(&bar, 0, &abort_flag, limit)) atomicExch(err, 1);
+}
+}  // namespace
+
+cs_status wait_selftest(long long limit_cycles, cudaStream_t stream) {
+  int* err = tc_error_word();
+  if (!err) return fail(CS_ECUDA, "cannot resolve the device error word");
+  wait_selftest_kernel<<<1, 32, 0, stream>>>(err, limit_cycles);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
 int* tc_error_word() {
   int* p = nullptr;
   if (cudaGetSymbolAddress((void**)&p, g_tc_error) != cudaSuccess) return nullptr;

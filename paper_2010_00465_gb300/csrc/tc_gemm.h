@@ -59,4 +59,8 @@ cs_status combine_f64(const float* hi, const float* lo, int64_t n, int64_t ld, d
 // Device word raised by a tensor-core kernel whose bounded wait expired.
 int* tc_error_word();
 
+// Launch one bounded wait that cannot be satisfied (limit in SM clocks); it
+// raises the device error word, which the next API call reports.
+cs_status wait_selftest(long long limit_cycles, cudaStream_t stream);
+
 }  // namespace cs
