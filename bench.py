@@ -366,13 +366,15 @@ def main():
 def forms(api, wsp):
     """The other precisions at n = 4096 and 8192 against the plain FP64 path on the same
     FP64 input: FP64 with every product emulated on the BF16 tensor cores,
-    split precision (Taylor chain on tensor cores) with native or emulated
-    FP64 double-angle products; each with its relative difference to the FP64
-    path stated beside it."""
+    split precision (Taylor chain as four-pass TF32 products) with native or
+    emulated FP64 double-angle products, and split precision on the BF16
+    tensor cores alone (four-slice chain products, eight-slice double-angle
+    products); each with its relative difference to the FP64 path stated
+    beside it."""
     import torch
     from paper_2010_00465_gb300 import inputs
     out = {}
-    precs = ("fp64", "fp64_emu", "split_tf32", "split_emu")
+    precs = ("fp64", "fp64_emu", "split_tf32", "split_emu", "split_bf16")
     for n_, nrm in [(N, 1.0), (N, 16.0), (N, 64.0), (2 * N, 1.0), (2 * N, 16.0), (2 * N, 64.0)]:
         A = torch.from_numpy(inputs.matrix(n_, "normal", nrm, index=2)).cuda()
         row = {}
@@ -402,37 +404,46 @@ def forms(api, wsp):
         del A, res
         torch.cuda.empty_cache()
     return {"n": [N, 2 * N], "family": "normal", "precisions": out, "fp64_emu_product": emu_product_form(api),
+            "bf16x4_product": emu_product_form(api, prec="split_bf16"),
             "batched": batched_form(api), "adjoint": adjoint_form(api), "cs": cs_form(api, wsp)}
 
 
-def emu_product_form(api, reps=5):
-    """One n = 4096 FP64 product emulated on the BF16 tensor cores: the
-    kernel's time from its own CUDA events, the 36 slice products it issues
-    against the measured BF16 peak, and the FP64 rate it stands for."""
+def emu_product_form(api, reps=5, prec="fp64_emu"):
+    """One n = 4096 product on the BF16 tensor cores from 7-bit slices: eight
+    slices (prec "fp64_emu", 36 slice products, FP64-class) or four (prec
+    "split_bf16", 10 slice products, FP32-class).  The kernel's time from its
+    own CUDA events, the slice products it issues against the measured BF16
+    peak, the FP64 rate it stands for, and its difference to the native FP64
+    product."""
     import torch
     from paper_2010_00465_gb300 import inputs
+    pairs = 36 if prec == "fp64_emu" else 10
     X = torch.from_numpy(inputs.matrix(N, "normal", None, index=1)).cuda()
     Y = torch.from_numpy(inputs.matrix(N, "normal", None, index=5)).cuda()
-    api.matmul(X, Y, "fp64_emu")
+    P = api.matmul(X, Y, prec)
+    P64 = api.matmul(X, Y, "fp64")
     torch.cuda.synchronize()
+    rel = float((P - P64).norm() / P64.norm())
+    del P, P64
     api.prof_reset()
     api.prof_enable(True)
     t0 = time.perf_counter()
     for _ in range(reps):
-        api.matmul(X, Y, "fp64_emu")
+        api.matmul(X, Y, prec)
     torch.cuda.synchronize()
     call_ms = (time.perf_counter() - t0) * 1e3 / reps
     api.prof_enable(False)
     ms, launches, work = api.prof_read("gemm_emu")
     kms = ms / max(launches, 1)
     pk, pk_kind = peaks()
-    issued = 36 * 2.0 * N ** 3 / (kms / 1e3) / 1e12
+    issued = pairs * 2.0 * N ** 3 / (kms / 1e3) / 1e12
     native = 2.0 * N ** 3
-    return {"n": N, "kernel_ms": kms, "call_ms_with_slicing_and_alloc": call_ms,
-            "fp64_equivalent_tflops": native / (kms / 1e3) / 1e12,
+    key = "ozaki_kernel" if pairs == 36 else "ozaki_kernel_s4"
+    return {"n": N, "prec": prec, "kernel_ms": kms, "call_ms_with_slicing_and_alloc": call_ms,
+            "fp64_equivalent_tflops": native / (kms / 1e3) / 1e12, "rel_diff_vs_fp64_product": rel,
             "roofline": {"bound": "tensor", "achieved": issued, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                         "frac": issued / pk["bf16_tflops"], "traffic": traffic_of("ozaki_kernel"),
-                         "note": "36 BF16 slice products per FP64 product; "
+                         "frac": issued / pk["bf16_tflops"], "traffic": traffic_of(key),
+                         "note": "%d BF16 slice products per product; " % pairs +
                          "peak = cuBLAS BF16 burst, " + pk_kind}}
 
 
@@ -597,9 +608,11 @@ def ncu_case(name):
         X = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
         api.matmul(X, X, "fp64")
     elif name == "gemm_emu":
-        # one n = 4096 FP64 product emulated on the BF16 tensor cores
+        # one n = 4096 FP64 product emulated on the BF16 tensor cores (eight
+        # slices), then one four-slice product
         X = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
         api.matmul(X, X, "fp64_emu")
+        api.matmul(X, X, "split_bf16")
     else:
         A = torch.from_numpy(inputs.matrix(2 * N, "normal", 1.0, index=1)).cuda()
         api.norm1(A)

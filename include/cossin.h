@@ -74,7 +74,15 @@ typedef enum {
   CS_FP64_EMU = 3,
   /* As CS_SPLIT_TF32, with the FP64 double-angle products emulated as in
    * CS_FP64_EMU (n <= 8192). */
-  CS_SPLIT_EMU = 4
+  CS_SPLIT_EMU = 4,
+  /* FP64 in and out; single table; every product on the BF16 tensor cores:
+   * the Taylor chain (steps 3-4) as BF16 multi-term products of four 7-bit
+   * slices per row / column (29 bits of each row / column maximum, the 10
+   * slice products with p + q <= 3, FP32-class: at most 2^-25 K max|X_i.|
+   * max|Y_.j| per entry), the double-angle steps as in CS_FP64_EMU; the
+   * norm and the choice of (m, s) in FP64.  cossin_matmul with this prec
+   * forms the four-slice product.  n <= 8192 (CS_EINVAL above). */
+  CS_SPLIT_BF16 = 5
 } cs_prec;
 
 /* What one call did. */
@@ -91,8 +99,8 @@ typedef struct {
  * Host-only; never touches the GPU. */
 cs_status cossin_workspace_size(int64_t n, cs_prec prec, size_t* bytes);
 
-/* Steps 1-2 only.  theta = ||A||_1 of the device matrix A_dev (FP64 for
- * CS_FP64 / CS_SPLIT_TF32, FP32 for CS_FP32), computed on the device with
+/* Steps 1-2 only.  theta = ||A||_1 of the device matrix A_dev (FP32 for
+ * CS_FP32, FP64 for every other prec), computed on the device with
  * FP64 accumulation; blocks until it is on the host.  Uses a small
  * library-owned device buffer (allocated on first use per device). */
 cs_status cossin_norm1(const void* A_dev, int64_t n, cs_prec prec, double* norm1,
@@ -185,11 +193,14 @@ cs_status cossin_cs(const void* A_dev, int64_t n, double t, cs_prec prec, void* 
 cs_status cossin_selftest_wait_timeout(cossin_stream_t stream);
 
 /* One product P = X Y (n x n, row-major) on the library's product kernel for
- * `prec`: the FP64 kernel for CS_FP64, the four-pass TF32 tensor-core kernel
- * for CS_FP32 (FP32 in and out) and CS_SPLIT_TF32 (FP64 in and out, computed
- * from the FP32 roundings of X and Y).  These are the products the method
- * counts (Pi_2m in Tables 1-2).  P must not overlap X or Y.  Allocates and
- * frees a stream-ordered workspace for the tensor-core kinds. */
+ * `prec`, the one its Taylor chain uses: the FP64 kernel for CS_FP64, the
+ * four-pass TF32 tensor-core kernel for CS_FP32 (FP32 in and out),
+ * CS_SPLIT_TF32 and CS_SPLIT_EMU (FP64 in and out, computed from the FP32
+ * roundings of X and Y), the eight-slice emulated product for CS_FP64_EMU
+ * and the four-slice BF16 product for CS_SPLIT_BF16 (FP64 in and out,
+ * n <= 8192 for these two).  These are the products the method counts (Pi_2m
+ * in Tables 1-2).  P must not overlap X or Y.  Allocates and frees a
+ * stream-ordered workspace for the tensor-core kinds. */
 cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec prec, void* P_dev,
                         cossin_stream_t stream);
 

@@ -13,7 +13,7 @@ _lib = None
 CS_OK, CS_EINVAL, CS_ENOMEM, CS_ENONFINITE, CS_ERANGE, CS_ECUDA, CS_ETIMEOUT = range(7)
 STATUS_NAMES = {0: "CS_OK", 1: "CS_EINVAL", 2: "CS_ENOMEM", 3: "CS_ENONFINITE", 4: "CS_ERANGE",
                 5: "CS_ECUDA", 6: "CS_ETIMEOUT"}
-CS_FP64, CS_FP32, CS_SPLIT_TF32, CS_FP64_EMU, CS_SPLIT_EMU = 0, 1, 2, 3, 4
+CS_FP64, CS_FP32, CS_SPLIT_TF32, CS_FP64_EMU, CS_SPLIT_EMU, CS_SPLIT_BF16 = 0, 1, 2, 3, 4, 5
 KERNEL_KINDS = {"norm1": 0, "gemm_f64": 1, "gemm_tf32": 2, "batched": 3, "adjoint": 4, "other": 5, "gemm_emu": 6}
 
 

@@ -14,9 +14,9 @@ from . import _lib
 from ._lib import CsInfo, check, lib
 
 PRECISIONS = {"fp64": _lib.CS_FP64, "fp32": _lib.CS_FP32, "split_tf32": _lib.CS_SPLIT_TF32,
-              "fp64_emu": _lib.CS_FP64_EMU, "split_emu": _lib.CS_SPLIT_EMU}
+              "fp64_emu": _lib.CS_FP64_EMU, "split_emu": _lib.CS_SPLIT_EMU, "split_bf16": _lib.CS_SPLIT_BF16}
 _DTYPE = {_lib.CS_FP64: torch.float64, _lib.CS_FP32: torch.float32, _lib.CS_SPLIT_TF32: torch.float64,
-          _lib.CS_FP64_EMU: torch.float64, _lib.CS_SPLIT_EMU: torch.float64}
+          _lib.CS_FP64_EMU: torch.float64, _lib.CS_SPLIT_EMU: torch.float64, _lib.CS_SPLIT_BF16: torch.float64}
 
 
 def _prec(prec, A=None) -> int:

@@ -122,12 +122,14 @@ Layout make_layout(int64_t n, int prec, bool with_outputs) {
   };
   L.norm_partial = take(sizeof(double) * (size_t)norm1_scratch_elems(n));
   L.norm_out = take(sizeof(double));
-  if (prec == CS_FP64 || prec == CS_FP64_EMU) {
+  if (f64_storage((cs_prec)prec)) {
     for (int w = 0; w < kWorkSlots; ++w) L.w[w] = take(sizeof(double) * n2);
     L.ping64[0] = take(sizeof(double) * 2 * n2);
     L.ping64[1] = take(sizeof(double) * 2 * n2);
-    if (prec == CS_FP64_EMU) {
-      L.ozaki_bytes = ozaki_dims(2 * n, n, n).total;  // the stacked double-angle product is the largest
+    if (prec != CS_FP64) {
+      // the stacked eight-slice double-angle product is the largest (the
+      // four-slice chain products of CS_SPLIT_BF16 need less)
+      L.ozaki_bytes = ozaki_dims(2 * n, n, n).total;
       L.ozaki = take(L.ozaki_bytes);
     }
   } else {
@@ -340,7 +342,7 @@ Epilogue<T> build_epilogue(const Step& st, T* const* hi, T* const* lo) {
 }
 
 cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, const Layout& L, const PlanSpec& P,
-                  const F64Product& prod, cudaStream_t stream) {
+                  const F64Product& chain, const F64Product& prod, cudaStream_t stream) {
   double* slot[SL_COUNT] = {};
   double* ping[2] = {(double*)(ws + L.ping64[0]), (double*)(ws + L.ping64[1])};
   const size_t n2 = (size_t)n * (size_t)n;
@@ -352,7 +354,7 @@ cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, co
   if (P.scale_into_w0) CS_CHECK(scale_f64(A, slot[W(0)], (int64_t)n2, P.input_scale, stream));
   for (const Step& st : P.steps) {
     Epilogue<double> e = build_epilogue<double>(st, slot, nullptr);
-    CS_CHECK(prod(slot[st.X], slot[st.Y], n, n, n, e, stream));
+    CS_CHECK(chain(slot[st.X], slot[st.Y], n, n, n, e, stream));
   }
   return square_f64(ping, n, s, C, S, stream, prod);
 }
@@ -363,17 +365,23 @@ cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, co
 // one stacked 2n x n x n product per step, ping-ponging between the buffers.
 cs_status F64Product::operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
                                  const Epilogue<double>& e, cudaStream_t stream) const {
-  if (emu_work) return gemm_f64_emu(X, Y, M, N, K, K, N, e, N, emu_work, emu_bytes, err, stream);
+  if (emu_work) return gemm_f64_emu(X, Y, M, N, K, K, N, e, N, emu_work, emu_bytes, err, stream, slices);
   return gemm_f64(X, Y, M, N, K, K, N, false, false, e, N, 1, 0, 0, 0, stream);
 }
 
 F64Product f64_product(cs_prec prec, char* ws, const Layout& L) {
   F64Product p;
-  if (prec == CS_FP64_EMU || prec == CS_SPLIT_EMU) {
+  if (uses_emu(prec)) {
     p.emu_work = ws + L.ozaki;
     p.emu_bytes = L.ozaki_bytes;
     p.err = tc_error_word();
   }
+  return p;
+}
+
+F64Product chain_product(cs_prec prec, char* ws, const Layout& L) {
+  F64Product p = f64_product(prec, ws, L);
+  if (prec == CS_SPLIT_BF16) p.slices = kOzakiSlicesSplit;
   return p;
 }
 
@@ -399,7 +407,9 @@ cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double*
   return CS_OK;
 }
 
-bool uses_emu(cs_prec p) { return p == CS_FP64_EMU || p == CS_SPLIT_EMU; }
+bool uses_emu(cs_prec p) { return p == CS_FP64_EMU || p == CS_SPLIT_EMU || p == CS_SPLIT_BF16; }
+
+bool f64_storage(cs_prec p) { return p == CS_FP64 || p == CS_FP64_EMU || p == CS_SPLIT_BF16; }
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
@@ -410,7 +420,8 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 size_t elem_size(cs_prec p) { return p == CS_FP32 ? sizeof(float) : sizeof(double); }
 
 cs_status check_prec(cs_prec prec) {
-  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32 && prec != CS_FP64_EMU && prec != CS_SPLIT_EMU)
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_SPLIT_TF32 && prec != CS_FP64_EMU && prec != CS_SPLIT_EMU &&
+      prec != CS_SPLIT_BF16)
     return fail(CS_EINVAL, "unknown precision");
   return CS_OK;
 }
@@ -494,8 +505,9 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   const int prods = products_of(m) + 2 * s;
   if (info) *info = cs_info{nrm, m, s, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
   const PlanSpec spec = cossin_spec(m, s, scale);
-  if (prec == CS_FP64 || prec == CS_FP64_EMU)
-    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, f64_product(prec, w, L), stream);
+  if (f64_storage(prec))
+    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, chain_product(prec, w, L),
+                   f64_product(prec, w, L), stream);
   return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
 
@@ -548,8 +560,9 @@ cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, voi
   const int prods = cs_family_products(f) + 2 * sg;
   if (info) *info = cs_info{normB, f, sg, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
   const PlanSpec spec = cs_spec(f, sg, t);
-  if (prec == CS_FP64 || prec == CS_FP64_EMU)
-    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, f64_product(prec, w, L), stream);
+  if (f64_storage(prec))
+    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, chain_product(prec, w, L),
+                   f64_product(prec, w, L), stream);
   return run_tf32(A, n, prec, C, S, w, L, spec, stream);
 }
 
@@ -632,7 +645,7 @@ cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, v
   if (cs::overlaps(P, bytes, X, bytes) || cs::overlaps(P, bytes, Y, bytes))
     return cs::fail(CS_EINVAL, "P must not overlap X or Y");
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == CS_FP64 || prec == CS_FP64_EMU) {
+  if (cs::f64_storage(prec)) {
     cs::Epilogue<double> e;
     e.n_out = 1;
     e.out[0] = (double*)P;
@@ -640,7 +653,8 @@ cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, v
     if (prec == CS_FP64)
       return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
     cs::F64Product prod;
-    prod.emu_bytes = cs::ozaki_dims(n, n, n).total;
+    prod.slices = prec == CS_SPLIT_BF16 ? cs::kOzakiSlicesSplit : cs::kOzakiSlices;
+    prod.emu_bytes = cs::ozaki_dims(n, n, n, 1, prod.slices).total;
     prod.err = cs::tc_error_word();
     if (!prod.err) return cs::fail(CS_ECUDA, "cannot resolve the device error word");
     CS_CUDA_CHECK(cudaMallocAsync(&prod.emu_work, prod.emu_bytes, st));

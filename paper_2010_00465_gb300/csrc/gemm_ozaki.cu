@@ -41,11 +41,20 @@
 // S (S + 1) / 2 = 36 BF16 products.  Exact for operands whose entries need
 // at most 57 bits below their row / column maximum (small integers, say).
 //
+// The same kernel with S = 4 is the BF16 multi-term product of the
+// split-precision form: 29 bits of each row / column maximum, 10 slice
+// products (levels 0..3, all summed exactly), at most 2^-25 K max|X_i.|
+// max|Y_.j| per entry; its level accumulators take 256 TMEM columns, so two
+// sets alternate between chunks and the MMAs of one chunk overlap the
+// epilogue's reading of the previous one.
+//
 // One CTA computes a 128 x 64 tile (S = 8):
 //   warp 0     TMA producer: all S slices of A (128 x 32) and of B^T (64 x 32)
-//              for one 32-wide k-block per stage, 64-byte swizzle, 2 stages;
+//              for one 32-wide k-block per stage, 64-byte swizzle, 192 KB of
+//              stages (2 for S = 8, 4 for S = 4);
 //   warp 1     allocates 512 TMEM columns (8 level accumulators of 64
-//              columns) and issues the MMAs (cta_group::1, M = 128, K = 16):
+//              columns; two sets of 4 for S = 4) and issues the MMAs
+//              (cta_group::1, M = 128, K = 16):
 //              per slice p of A, N = 128 instructions that pair the slices q,
 //              q + 1 of B into the accumulators of levels p + q, p + q + 1
 //              (16 per k-step, plus 4 of N = 64 for the odd pair left), the
@@ -74,7 +83,6 @@ namespace {
 
 using namespace ptx;
 
-constexpr int S = kOzakiSlices;        // slices per operand
 constexpr int BM = 128;
 constexpr int BN = 64;
 #ifndef COSSIN_OZAKI_BK
@@ -86,21 +94,25 @@ constexpr int BN = 64;
 constexpr int BK = COSSIN_OZAKI_BK;
 constexpr int kSwizzleBytes = BK * 2;  // one swizzle row = one stage row
 constexpr int kChunkKb = 512 / BK;     // k-blocks per 512-k accumulator chunk
-constexpr int kAcc = S;               // one accumulator of BN columns per level p + q < S
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kCols = BN / 2;          // columns per epilogue warp
 constexpr int kABytes = BM * BK * 2;   // one A slice of a stage
 constexpr int kBBytes = BN * BK * 2;   // one B slice of a stage
-constexpr int kStageBytes = S * (kABytes + kBBytes);
-constexpr int kStages = BK == 16 ? 4 : 2;
 constexpr int kGroupM = 8;             // M tiles per raster group
-constexpr int kSmem = kStages * kStageBytes + 32 * (2 * (BN / 2) + 1) * 8 + 1024;  // stages + epilogue staging
-constexpr uint32_t kTmemCols = 512;
-static_assert(kAcc * BN <= (int)kTmemCols, "TMEM columns");
-static_assert(kSmem <= 227 * 1024, "shared memory");
 constexpr int kStageRows = 32;          // rows of the tile staged per epilogue round
 constexpr int kLd = 2 * kCols + 1;      // staging row pitch (doubles)
+// Per slice count S: all S slices of A and B^T of one k-block form a stage,
+// 192 KB of stages are in flight (2 stages for S = 8, 4 for S = 4), and the
+// S level accumulators of BN columns fill S BN TMEM columns.
+__host__ __device__ constexpr int stage_bytes(int S) { return S * (kABytes + kBBytes); }
+__host__ __device__ constexpr int num_stages(int S) { return (192 * 1024) / stage_bytes(S); }
+__host__ __device__ constexpr int smem_bytes(int S) {
+  return num_stages(S) * stage_bytes(S) + kStageRows * kLd * 8 + 1024;  // stages + epilogue staging
+}
+static_assert(smem_bytes(kOzakiSlices) <= 227 * 1024 && smem_bytes(kOzakiSlicesSplit) <= 227 * 1024,
+              "shared memory");
+static_assert(kOzakiSlices * BN == 512 && kOzakiSlicesSplit * BN == 256, "TMEM columns: a power of two <= 512");
 // Instruction descriptors, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 // An N = 2 BN instruction reads the B slices q and q + 1, which lie next to
@@ -143,6 +155,7 @@ __device__ __forceinline__ int line_exponent(double mx) {
 // a_p = round(R_p / 2^(49 - 7p)), R_{p+1} = R_p - a_p 2^(49 - 7p), the last
 // digit taking the exact remainder: |a_0| <= 128, |a_p| <= 64.  Slice p is
 // stored as the BF16 value a_p 2^(-7p) (exact).
+template <int S>
 __device__ __forceinline__ void cut(double x, int e, __nv_bfloat16 (&q)[S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int eb = (int)((bits >> 52) & 0x7FF);
@@ -229,6 +242,7 @@ __global__ void col_exp_kernel(const double* __restrict__ Y, int64_t ld, const u
 // Left operand: out[b][s][r][k] (row-major, K contiguous) for r < rows_pad,
 // k < ldk, matrix b = blockIdx.y of a batch; rows >= rows and k >= cols are
 // zero.
+template <int S>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
                                                          int64_t ld, const int* __restrict__ ex,
                                                          __nv_bfloat16* __restrict__ out, int64_t rows_pad,
@@ -250,6 +264,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
 // Right operand Y (rows = K, cols = N, row-major): out[s][c][k], the
 // transposed slices (K contiguous) for c < cols_pad, k < ldk, through a
 // 32 x 32 shared-memory tile per slice.
+template <int S>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int64_t cols,
                                                          int64_t ld, const int* __restrict__ ex,
                                                          __nv_bfloat16* __restrict__ out, int64_t cols_pad,
@@ -289,6 +304,7 @@ __device__ __forceinline__ double pow2(int e) {
 // so the producer and the MMA warp run on into the next tile while the
 // epilogue warps finish the previous one (its accumulators are released
 // before the FP64 epilogue, which stages through its own shared memory).
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int M, int N, int K,
                  int Mpad, int Npad, const int* __restrict__ ex_all, const int* __restrict__ fx_all,
@@ -296,13 +312,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const double* __restrict__ xd_all, const double* __restrict__ yd_all, int64_t ldo,
                  const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse,
                  int batch) {
+  constexpr int kAcc = S;  // one accumulator of BN columns per level p + q < S
+  constexpr int kStageBytes = stage_bytes(S);
+  constexpr int kStages = num_stages(S);
+  // Two sets of level accumulators when they fit in the 512 TMEM columns
+  // (S = 4): the MMAs of chunk c + 1 run while the epilogue drains chunk c.
+  constexpr int kBufs = 2 * S * BN <= 512 ? 2 : 1;
+  constexpr uint32_t kTmemCols = (uint32_t)(S * BN * kBufs);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   double* stage_tile = (double*)(smem + kStages * kStageBytes);  // kStageRows x kLd doubles
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
-  __shared__ __align__(8) uint64_t chunk_bar;
-  __shared__ __align__(8) uint64_t free_bar[kAcc];
+  __shared__ __align__(8) uint64_t chunk_bar[kBufs];
+  __shared__ __align__(8) uint64_t free_bar[kBufs][kAcc];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int stop_epi;
@@ -332,8 +355,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&chunk_bar, 1);
-    for (int a = 0; a < kAcc; ++a) mbar_init(&free_bar[a], kEpiWarps);
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(&chunk_bar[b], 1);
+      for (int a = 0; a < kAcc; ++a) mbar_init(&free_bar[b][a], kEpiWarps);
+    }
     abort_flag = 0;
     stop_epi = 0;
     kb_consumed = 0;
@@ -395,7 +420,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_lo = ((smem_u32(smem + st * kStageBytes) & 0x3FFFFu) >> 4) | (1u << 16);
             const uint32_t b_lo = a_lo + (uint32_t)((S * kABytes) >> 4);
             const bool chunk_start = kk == 0;
-            const bool wait_free = kk == 0 && cg > 0;
+            // chunk cg accumulates into set cg % kBufs, which chunk
+            // cg - kBufs used before; the epilogue must have read that one
+            const int buf = cg % kBufs;
+            const uint32_t acc0 = tmem + (uint32_t)(buf * S * BN);
+            const bool wait_free = kk == 0 && cg >= kBufs;
+            const uint32_t free_par = (uint32_t)((cg / kBufs - 1) & 1);
             bool stop = false;
 #pragma unroll
             for (int j = 0; j < BK / 16 && !stop; ++j) {  // K = 16 bf16 (32 bytes) per instruction
@@ -412,22 +442,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                   // its accumulators, after the epilogue has read them
                   const bool restart = chunk_start && j == 0 && p == 0;
                   if (restart && wait_free) {
-                    if (!mbar_wait(&free_bar[q], (cg - 1) & 1, &abort_flag) ||
-                        !mbar_wait(&free_bar[q + 1], (cg - 1) & 1, &abort_flag)) {
+                    if (!mbar_wait(&free_bar[buf][q], free_par, &abort_flag) ||
+                        !mbar_wait(&free_bar[buf][q + 1], free_par, &abort_flag)) {
                       abort_flag = 1;
                       stop = true;
                       break;
                     }
                     tc_fence_after();
                   }
-                  mma_bf16(tmem + (uint32_t)((p + q) * BN), ad, bd, kIdesc2, restart ? 0u : 1u);
+                  mma_bf16(acc0 + (uint32_t)((p + q) * BN), ad, bd, kIdesc2, restart ? 0u : 1u);
                 }
                 if (stop) break;
                 if ((S - p) & 1) {  // the last pair (p, S - 1 - p) alone, level S - 1
                   const int q = S - 1 - p;
                   const uint64_t bd =
                       ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
-                  mma_bf16(tmem + (uint32_t)((S - 1) * BN), ad, bd, kIdesc1, 1u);
+                  mma_bf16(acc0 + (uint32_t)((S - 1) * BN), ad, bd, kIdesc1, 1u);
                 }
               }
             }
@@ -435,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(&empty_bar[st]);
             kb_consumed = g + 1;
           }
-          mma_commit(&chunk_bar);  // also tracks the MMAs of an aborted chunk
+          mma_commit(&chunk_bar[cg % kBufs]);  // also tracks the MMAs of an aborted chunk
           chunks_committed = cg + 1;
         }
       }
@@ -460,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < num_chunks; ++c, ++cg) {
         int w = 1;
         if (lane == 0) {
-          w = mbar_wait(&chunk_bar, cg & 1, &abort_flag) && !abort_flag;
+          w = mbar_wait(&chunk_bar[cg % kBufs], (cg / kBufs) & 1, &abort_flag) && !abort_flag;
           if (!w) abort_flag = 1;
         }
         w = __shfl_sync(0xffffffffu, w, 0);
@@ -472,13 +502,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int a = 0; a < kAcc; ++a) {
           uint32_t v0[16], v1[16];
-          const uint32_t tq = tmem + lane_off + (uint32_t)(a * BN + col0);
+          const uint32_t tq = tmem + lane_off + (uint32_t)((cg % kBufs) * S * BN + a * BN + col0);
           tmem_ld16(tq, v0);
           tmem_ld16(tq + 16u, v1);
           tmem_ld_wait();
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&free_bar[a]);
+          if (lane == 0) mbar_arrive(&free_bar[cg % kBufs][a]);
           const int e = 7 * a < 35 ? 7 * a : 35;  // value * 2^e is an integer (rounded for levels > 5)
           const float sc = __int_as_float((127 + e) << 23);
           const long long unit = 1LL << (35 - e);
@@ -576,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1 && lane == 0 && chunks_committed > 0) {
       volatile int never = 0;
       const int c = chunks_committed - 1;
-      mbar_wait(&chunk_bar, c & 1, &never);
+      mbar_wait(&chunk_bar[c % kBufs], (c / kBufs) & 1, &never);
     }
     if (threadIdx.x == 0) atomicExch(err, 1);
   }
@@ -630,13 +660,14 @@ int grid_for(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256,
 
 }  // namespace
 
-OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch) {
+OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch, int slices) {
   OzakiDims d;
   d.Mpad = (M + BM - 1) / BM * BM;
   d.Npad = (N + BN - 1) / BN * BN;
   d.ldk = (K + 31) / 32 * 32;  // the slicing kernels work in 32 x 32 tiles
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t nb = (size_t)(batch > 0 ? batch : 1);
+  const size_t S = (size_t)(slices > 0 ? slices : kOzakiSlices);
   d.a_bytes = al(nb * S * d.Mpad * d.ldk * 2);
   d.b_bytes = al(nb * S * d.Npad * d.ldk * 2);
   d.ex_bytes = al(nb * sizeof(int) * (size_t)d.Mpad);
@@ -648,20 +679,15 @@ OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch) {
   return d;
 }
 
-cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx,
-                               int64_t ldy, const Epilogue<double>& epi, int64_t ldo, int64_t batch, int64_t bsx,
-                               int64_t bsy, int64_t bse, void* work, size_t work_bytes, int* err,
-                               cudaStream_t stream) {
-  if (M <= 0 || N <= 0 || batch <= 0) return CS_OK;
-  if (M > (1 << 20) || N > (1 << 20) || K > (1 << 20)) return fail(CS_EINVAL, "gemm_f64_emu: size too large");
-  if (K <= 0 || N != K) return fail(CS_EINVAL, "gemm_f64_emu: the right operand must be square");
-  if (K > kOzakiMaxK) return fail(CS_EINVAL, "gemm_f64_emu: K above 8192 (the int64 sums would overflow)");
-  if (batch > 65535) return fail(CS_EINVAL, "gemm_f64_emu: batch above 65535");
-  const OzakiDims d = ozaki_dims(M, N, K, batch);
-  if (!work || work_bytes < d.total || ((uintptr_t)work & 255)) return fail(CS_EINVAL, "gemm_f64_emu: workspace");
-  if (!err) return fail(CS_ECUDA, "gemm_f64_emu: no device error word");
-  if (batch * S * d.Mpad > INT32_MAX || batch * S * d.Npad > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: too large");
-  char* w = (char*)work;
+namespace {
+
+// Slicing kernels and the product kernel for S slices (arguments checked by
+// the caller).
+template <int S>
+cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
+                     const Epilogue<double>& epi, int64_t ldo, int64_t batch, int64_t bsx, int64_t bsy, int64_t bse,
+                     const OzakiDims& d, char* w, int* err, cudaStream_t stream) {
+  constexpr int kSmem = smem_bytes(S);
   __nv_bfloat16* a_sl = (__nv_bfloat16*)w;
   __nv_bfloat16* b_sl = (__nv_bfloat16*)(w + d.a_bytes);
   int* ex = (int*)(w + d.a_bytes + d.b_bytes);
@@ -678,8 +704,8 @@ cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int6
         Y, K, N, ldy, colmax, bsy, d.Npad);
     col_exp_kernel<<<dim3((unsigned)((N + 255) / 256), nb), 256, 0, stream>>>(Y, ldy, colmax, N, fx, yd, bsy, d.Npad);
     const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(d.Mpad * d.ldk), 152 * 16 / batch + 1));
-    slice_rows_kernel<<<dim3(sgrid, nb), 256, 0, stream>>>(X, M, K, ldx, ex, a_sl, d.Mpad, d.ldk, bsx);
-    slice_cols_kernel<<<dim3((unsigned)(d.Npad / 32), (unsigned)(d.ldk / 32), nb), 256, 0, stream>>>(
+    slice_rows_kernel<S><<<dim3(sgrid, nb), 256, 0, stream>>>(X, M, K, ldx, ex, a_sl, d.Mpad, d.ldk, bsx);
+    slice_cols_kernel<S><<<dim3((unsigned)(d.Npad / 32), (unsigned)(d.ldk / 32), nb), 256, 0, stream>>>(
         Y, K, N, ldy, fx, b_sl, d.Npad, d.ldk, bsy);
     CS_CUDA_CHECK(cudaGetLastError());
   }
@@ -689,7 +715,7 @@ cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int6
   CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, BN));
   static bool attr_set = false;
   if (!attr_set) {
-    CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr_set = true;
   }
   const int64_t tiles = (d.Npad / BN) * (d.Mpad / BM) * batch;
@@ -698,16 +724,41 @@ cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int6
   CS_CUDA_CHECK(cudaGetDevice(&dev));
   CS_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms > 0 ? sms : 1);
-  ozaki_kernel<<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex, fx,
-                                                  X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse, (int)batch);
+  ozaki_kernel<S><<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex,
+                                                     fx, X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse,
+                                                     (int)batch);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
 
+}  // namespace
+
+cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx,
+                               int64_t ldy, const Epilogue<double>& epi, int64_t ldo, int64_t batch, int64_t bsx,
+                               int64_t bsy, int64_t bse, void* work, size_t work_bytes, int* err,
+                               cudaStream_t stream, int slices) {
+  if (slices != kOzakiSlices && slices != kOzakiSlicesSplit) return fail(CS_EINVAL, "gemm_f64_emu: slices must be 8 or 4");
+  if (M <= 0 || N <= 0 || batch <= 0) return CS_OK;
+  if (M > (1 << 20) || N > (1 << 20) || K > (1 << 20)) return fail(CS_EINVAL, "gemm_f64_emu: size too large");
+  if (K <= 0 || N != K) return fail(CS_EINVAL, "gemm_f64_emu: the right operand must be square");
+  if (K > kOzakiMaxK) return fail(CS_EINVAL, "gemm_f64_emu: K above 8192 (the int64 sums would overflow)");
+  if (batch > 65535) return fail(CS_EINVAL, "gemm_f64_emu: batch above 65535");
+  const OzakiDims d = ozaki_dims(M, N, K, batch, slices);
+  if (!work || work_bytes < d.total || ((uintptr_t)work & 255)) return fail(CS_EINVAL, "gemm_f64_emu: workspace");
+  if (!err) return fail(CS_ECUDA, "gemm_f64_emu: no device error word");
+  if (batch * slices * d.Mpad > INT32_MAX || batch * slices * d.Npad > INT32_MAX)
+    return fail(CS_EINVAL, "gemm_f64_emu: too large");
+  if (slices == kOzakiSlicesSplit)
+    return launch_emu<kOzakiSlicesSplit>(X, Y, M, N, K, ldx, ldy, epi, ldo, batch, bsx, bsy, bse, d, (char*)work, err,
+                                         stream);
+  return launch_emu<kOzakiSlices>(X, Y, M, N, K, ldx, ldy, epi, ldo, batch, bsx, bsy, bse, d, (char*)work, err,
+                                  stream);
+}
+
 cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
                        const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
-                       cudaStream_t stream) {
-  return gemm_f64_emu_batched(X, Y, M, N, K, ldx, ldy, epi, ldo, 1, 0, 0, 0, work, work_bytes, err, stream);
+                       cudaStream_t stream, int slices) {
+  return gemm_f64_emu_batched(X, Y, M, N, K, ldx, ldy, epi, ldo, 1, 0, 0, 0, work, work_bytes, err, stream, slices);
 }
 
 namespace {

@@ -120,7 +120,8 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
                         cs_info* infos_host, cudaStream_t stream, bool emu = false);
 cs_status check_prec(cs_prec prec);
-bool uses_emu(cs_prec p);  // CS_FP64_EMU, CS_SPLIT_EMU: FP64 products emulated on the tensor cores
+bool uses_emu(cs_prec p);      // CS_FP64_EMU, CS_SPLIT_EMU, CS_SPLIT_BF16: sliced BF16 tensor-core products
+bool f64_storage(cs_prec p);  // CS_FP64, CS_FP64_EMU, CS_SPLIT_BF16: the FP64 executor (FP64 intermediates)
 size_t elem_size(cs_prec p);
 bool overlaps(const void* a, size_t na, const void* b, size_t nb);
 

@@ -8,12 +8,12 @@
 
 namespace cs {
 
-#ifndef COSSIN_OZAKI_SLICES
-#define COSSIN_OZAKI_SLICES 8
-#endif
-// 7-bit slices per operand: 57 bits of each row / column maximum (8 slices;
-// one 64-column TMEM accumulator per level, so at most 8)
-constexpr int kOzakiSlices = COSSIN_OZAKI_SLICES;
+// 7-bit slices per operand.  8 slices carry 57 bits of each row / column
+// maximum (FP64-class products, one 64-column TMEM accumulator per level, so
+// at most 8); 4 slices carry 29 bits (FP32-class products for the Taylor
+// chain of the split-precision form).
+constexpr int kOzakiSlices = 8;
+constexpr int kOzakiSlicesSplit = 4;
 
 constexpr int64_t kOzakiMaxK = 8192;  // inner dimension limit of the int64 sums
 
@@ -24,24 +24,25 @@ struct OzakiDims {
   size_t a_bytes = 0, b_bytes = 0, ex_bytes = 0, fx_bytes = 0, colmax_bytes = 0, xd_bytes = 0, yd_bytes = 0;
   size_t total = 0;
 };
-OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch = 1);
+OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch = 1, int slices = kOzakiSlices);
 
 // P = X Y (X: M x K, Y: K x K, row-major FP64; M = K or the stacked 2K) with
 // the fused FP64 epilogue of gemm_f64 (stacked mode included); the entries
 // X[r][r mod K] and Y[c][c] are added exactly in FP64, the rest is emulated.
-// `work` holds ozaki_dims(M, N, K).total bytes (256-byte aligned).  A
-// bounded wait that expires raises *err.
+// `work` holds ozaki_dims(M, N, K, 1, slices).total bytes (256-byte
+// aligned); `slices` is kOzakiSlices or kOzakiSlicesSplit.  A bounded wait
+// that expires raises *err.
 cs_status gemm_f64_emu(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx, int64_t ldy,
                        const Epilogue<double>& epi, int64_t ldo, void* work, size_t work_bytes, int* err,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int slices = kOzakiSlices);
 
 // The same over `batch` independent products: operand b at X + b bsx and
 // Y + b bsy, every epilogue matrix at + b bse; `work` holds
-// ozaki_dims(M, N, K, batch).total bytes.
+// ozaki_dims(M, N, K, batch, slices).total bytes.
 cs_status gemm_f64_emu_batched(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx,
                                int64_t ldy, const Epilogue<double>& epi, int64_t ldo, int64_t batch, int64_t bsx,
                                int64_t bsy, int64_t bse, void* work, size_t work_bytes, int* err,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int slices = kOzakiSlices);
 
 // dst_b = src_b^T for `batch` n x n row-major FP64 matrices at stride bs (dst
 // must not overlap src).

@@ -8,6 +8,7 @@
 #include <utility>
 
 #include "internal.cuh"
+#include "ozaki.h"
 #include <vector>
 
 namespace cs {
@@ -66,7 +67,7 @@ struct Layout {
   size_t a4[4] = {};
   size_t w4[kWorkSlots][4] = {};
   size_t ping4[2][4] = {};
-  size_t ozaki = 0, ozaki_bytes = 0;  // scratch of one emulated product (CS_FP64_EMU)
+  size_t ozaki = 0, ozaki_bytes = 0;  // scratch of one emulated product (CS_FP64_EMU, *_EMU, *_BF16)
   size_t out_c = 0, out_s = 0;  // n x n C and S of the precision's type (with_outputs)
   size_t total = 0;
 };
@@ -74,16 +75,20 @@ struct Layout {
 Layout make_layout(int64_t n, int prec, bool with_outputs = false);
 
 // How the FP64 executors form a product P = X Y (row-major, X: M x K, Y: K x N)
-// with its epilogue: natively (gemm_f64) or, with emu_work set, emulated on
-// the tensor cores (gemm_f64_emu) using that scratch.
+// with its epilogue: natively (gemm_f64) or, with emu_work set, on the BF16
+// tensor cores (gemm_f64_emu) with `slices` slices, using that scratch.
 struct F64Product {
   void* emu_work = nullptr;
   size_t emu_bytes = 0;
   int* err = nullptr;
+  int slices = kOzakiSlices;
   cs_status operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
                        const Epilogue<double>& e, cudaStream_t stream) const;
 };
+// The product of the double-angle steps for `prec` (the Taylor chain's, too,
+// but for CS_SPLIT_BF16, whose chain takes chain_product).
 F64Product f64_product(cs_prec prec, char* ws, const Layout& L);
+F64Product chain_product(cs_prec prec, char* ws, const Layout& L);
 
 // Double-angle steps in FP64 on the stacked buffers ping[2] (each 2n x n):
 // starts from [C; S] in ping[0]; the last step writes C and S.

@@ -101,16 +101,23 @@ def test_emulated_precisions_host_checks(L):
     """The emulated-FP64 precisions add their slice scratch to the workspace
     and accept n <= 8192 only (the int64 level sums), refused before any
     device work."""
-    for p in ("fp64_emu", "split_emu"):
-        assert api.workspace_size(1024, p) > api.workspace_size(1024, "fp64" if p == "fp64_emu" else "split_tf32")
+    base = {"fp64_emu": "fp64", "split_emu": "split_tf32", "split_bf16": "fp64"}
+    for p in ("fp64_emu", "split_emu", "split_bf16"):
+        assert api.workspace_size(1024, p) > api.workspace_size(1024, base[p])
         assert api.workspace_size(8192, p) > 0
         with pytest.raises(_lib.CossinError) as e:
             api.workspace_size(8193, p)
         assert e.value.status == _lib.CS_EINVAL
+    # the four-slice chain products share the eight-slice scratch
+    assert api.workspace_size(1024, "split_bf16") == api.workspace_size(1024, "fp64_emu")
     assert api.workspace_size(8193, "fp64") > 0
     assert api.unitary_workspace_size(100, "fp64") > api.workspace_size(100, "fp64")
     with pytest.raises(_lib.CossinError):
-        api.workspace_size(16, 5)
+        api.workspace_size(16, 6)
+    # the adjoint has no split-precision form
+    nul = ctypes.c_void_p(0)
+    assert L.cossin_backward_ex(1, 4, nul, nul, nul, nul, nul, nul, -1, -1, _lib.CS_SPLIT_BF16, None,
+                                nul) == _lib.CS_EINVAL
 
 
 def test_cs_and_unitary_argument_errors_before_any_gpu_work(L):

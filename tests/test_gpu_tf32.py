@@ -2,9 +2,11 @@
 
 CS_FP32: FP32 in/out, single table, every product a four-pass TF32 tcgen05
 product; CS_SPLIT_TF32: FP64 in/out, single table, Taylor chain on tensor
-cores, double-angle steps in FP64.  Both are compared with the oracle run on
-the same input (FP32 inputs upcast exactly) at the same (2m, s) with the single
-table; the bound is 2e-5 relative Frobenius for ||A||_1 <= 64.
+cores, double-angle steps in FP64 (CS_SPLIT_EMU: those emulated on the BF16
+tensor cores); CS_SPLIT_BF16: the Taylor chain as four-slice BF16 products,
+the double-angle steps as eight-slice ones.  All are compared with the oracle
+run on the same input (FP32 inputs upcast exactly) at the same (2m, s) with
+the single table; the bound is 2e-5 relative Frobenius for ||A||_1 <= 64.
 """
 import numpy as np
 import pytest
@@ -55,7 +57,7 @@ def run(A, prec, **kw):
     return C.double().cpu().numpy(), S.double().cpu().numpy(), info
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("n", [1, 5, 33, 64, 100, 128, 129, 255, 256, 257, 300])
 @pytest.mark.parametrize("nrm", [2.0 ** -6, 2.0 ** -4, 1.0, 8.0, 64.0])
 def test_matches_oracle(prec, n, nrm):
@@ -69,7 +71,7 @@ def test_matches_oracle(prec, n, nrm):
     assert relfro(S, So) <= tol32(n, nrm), relfro(S, So)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("m", [4, 8, 9, 16, 24])
 @pytest.mark.parametrize("s", [0, 2])
 def test_every_family_forced(prec, m, s):
@@ -81,7 +83,7 @@ def test_every_family_forced(prec, m, s):
     assert relfro(C, Co) <= TOL32 and relfro(S, So) <= TOL32
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("family", ["symmetric", "triangular", "uniform01", "uniform_pm", "nilpotent"])
 def test_families(prec, family):
     for nrm in (2.0 ** -4, 1.0, 8.0, 64.0):
@@ -95,7 +97,7 @@ def test_families(prec, family):
         assert relfro(C, Co) <= t and relfro(S, So) <= t, (family, nrm)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 def test_accuracy_against_double_oracle(prec):
     """Against the true function (oracle, double table) the error stays FP32-level."""
     for nrm in (0.1, 1.0, 8.0, 64.0):
@@ -144,7 +146,7 @@ def _block_case(n, block, nrm, index):
     return A, blocks, perm
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("nrm", [2.0 ** -4, 1.0, 8.0, 64.0])
 def test_full_size_block_diagonal(prec, nrm):
     n, block = 4096, 64
@@ -162,7 +164,7 @@ def test_full_size_block_diagonal(prec, nrm):
 
 _FULL_CASES = [("normal", 2.0 ** -4), ("normal", 1.0), ("normal", 8.0), ("normal", 64.0), ("symmetric", 8.0),
                ("triangular", 8.0)]
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("family,nrm", _FULL_CASES)
 def test_full_size_against_fp64_path(prec, family, nrm):
     """n = 4096 dense: the FP32 and split paths against the FP64 path, which
@@ -179,7 +181,7 @@ def test_full_size_against_fp64_path(prec, family, nrm):
     assert ec <= TOL32 and es <= TOL32, (prec, family, nrm, ec, es)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("family,nrm", [("normal", 8.0), ("normal", 64.0), ("triangular", 8.0), ("symmetric", 8.0)])
 def test_full_size_dense_properties(prec, family, nrm):
     n = 4096
@@ -199,7 +201,7 @@ def test_full_size_dense_properties(prec, family, nrm):
         assert float((Cd - Cr).norm() / Cr.norm()) <= TOL32
 
 
-@pytest.mark.parametrize("prec", ["split_tf32", "split_emu"])
+@pytest.mark.parametrize("prec", ["split_tf32", "split_emu", "split_bf16"])
 @pytest.mark.parametrize("nrm", [1.0, 64.0])
 def test_split_n8192_block_diagonal(prec, nrm):
     """The split workload's larger order, n = 8192: a permuted block-diagonal
