@@ -99,7 +99,8 @@ cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64
                    cudaStream_t stream);
 
 // ||A||_1 for an FP64 or FP32 matrix into a device double (*out_dev).
-// partial_dev: ceil(n / 8192)... scratch of norm1_scratch_elems(n) doubles.
+// partial_dev: scratch of norm1_scratch_elems(n) doubles (column partial sums,
+// pass-2 block maxima and a ticket word).
 int64_t norm1_scratch_elems(int64_t n);
 cs_status norm1_f64(const double* A, int64_t n, double* partial_dev, double* out_dev,
                     cudaStream_t stream);

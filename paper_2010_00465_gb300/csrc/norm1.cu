@@ -2,13 +2,24 @@
 // (Sec. 4: the algorithm is driven by the matrix 1-norm).
 //
 // Row-major A, so a column sum walks down a stride-n column.  Pass 1 gives
-// each thread one column and a chunk of ROWS rows: a warp reads 32 adjacent
+// each thread one column and a chunk of kRows rows: a warp reads 32 adjacent
 // columns of one row per step (coalesced), and every block writes its column
 // partial sums for its row chunk.  Pass 2 adds the partials of each column in
 // a fixed order (deterministic), then takes the maximum with warp shuffles and
 // one shared-memory round per block, the last block reducing the block maxima.
-// Accumulation is FP64 for both input types.  A NaN
-// anywhere makes the result NaN; Inf stays Inf.
+//
+// GB300 adds FP64 at 2 per clock per SM, which would cap pass 1 below the HBM
+// rate (one add per element), so pass 1 sums on the integer pipes: each
+// |a| = m 2^(e - bias) (integer significand m, biased exponent e) is aligned
+// to the largest exponent E seen so far in the chunk with g guard bits
+// (g = 3 for FP64, 32 for FP32, so that m 2^g < 2^56), m 2^(g - (E - e))
+// truncated to an integer, and added into an int64 sum (below 2^62 for 64
+// rows); the sum is shifted when E grows.  Each term and
+// each shift drops less than 2^-55 of the chunk's largest element, so the
+// chunk sum is within 2^-48 relative of the exact one before its single
+// conversion to FP64.  A chunk holding an Inf or NaN is summed again in FP64
+// (a NaN anywhere makes the result NaN; Inf stays Inf).  Pass 2 and the
+// maxima are FP64.
 #include <math.h>
 
 #include <mutex>
@@ -20,10 +31,33 @@ namespace {
 
 constexpr int kCols = 256;  // threads (= columns) per block in pass 1
 constexpr int kRows = 64;   // rows per chunk in pass 1
+static_assert(kRows <= 64, "the int64 chunk sums hold at most 64 terms below 2^56");
+
+// Bit layout of the element type: significand bits (without the implicit
+// one), exponent field width and bias.
+template <typename T>
+struct Layout754;
+template <>
+struct Layout754<double> {
+  using U = unsigned long long;
+  static constexpr int kMant = 52, kExpMax = 0x7FF, kBias = 1075;  // |x| = m 2^(e - 1075)
+  static constexpr int kGuard = 3;                                  // m 2^kGuard < 2^56
+  __device__ static U bits(const double* p) { return (U)__double_as_longlong(__ldg(p)); }
+};
+template <>
+struct Layout754<float> {
+  using U = unsigned int;
+  static constexpr int kMant = 23, kExpMax = 0xFF, kBias = 150;  // |x| = m 2^(e - 150)
+  static constexpr int kGuard = 32;                               // m 2^kGuard < 2^56
+  __device__ static U bits(const float* p) { return (U)__float_as_uint(__ldg(p)); }
+};
+
+__device__ __forceinline__ unsigned long long shr(unsigned long long x, int k) { return k > 63 ? 0ULL : x >> k; }
 
 template <typename T>
 __global__ void __launch_bounds__(kCols) colsum_partial(const T* __restrict__ A, int64_t n,
                                                         double* __restrict__ partial, unsigned int* __restrict__ ticket) {
+  using L = Layout754<T>;
   // pass 2 counts its blocks on this word; pass 1 runs first on the stream
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ticket = 0u;
   const int64_t col = (int64_t)blockIdx.x * kCols + threadIdx.x;
@@ -31,17 +65,54 @@ __global__ void __launch_bounds__(kCols) colsum_partial(const T* __restrict__ A,
   if (col >= n) return;
   const int64_t r1 = min(r0 + (int64_t)kRows, n);
   const T* p = A + r0 * n + col;
-  double acc = 0.0;
+  unsigned long long sum = 0;  // sum of m 2^(3 - (E - e))
+  int E = 1;                   // alignment exponent (the smallest biased exponent of a finite value)
+  bool special = false;        // an Inf or NaN in the chunk
+  // one element: significand with the implicit one, effective exponent
+  auto unpack = [](typename L::U b, unsigned long long& m, int& e) {
+    const int eb = (int)((b >> L::kMant) & (typename L::U)L::kExpMax);
+    m = (unsigned long long)(b & (((typename L::U)1 << L::kMant) - 1));
+    if (eb) m |= 1ULL << L::kMant;
+    e = eb ? eb : 1;
+  };
   int64_t r = r0;
   // eight independent loads in flight per thread
   for (; r + 8 <= r1; r += 8, p += 8 * n) {
-    double v[8];
+    typename L::U v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = fabs((double)__ldg(p + u * n));
+    for (int u = 0; u < 8; ++u) v[u] = L::bits(p + u * n);
+    unsigned long long m[8];
+    int e[8];
+    int emax = E;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc += v[u];
+    for (int u = 0; u < 8; ++u) {
+      unpack(v[u], m[u], e[u]);
+      special |= e[u] == L::kExpMax;
+      emax = max(emax, e[u]);
+    }
+    sum = shr(sum, emax - E);
+    E = emax;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += shr(m[u] << L::kGuard, E - e[u]);
   }
-  for (; r < r1; ++r, p += n) acc += fabs((double)__ldg(p));
+  for (; r < r1; ++r, p += n) {
+    unsigned long long m;
+    int e;
+    unpack(L::bits(p), m, e);
+    special |= e == L::kExpMax;
+    if (e > E) {
+      sum = shr(sum, e - E);
+      E = e;
+    }
+    sum += shr(m << L::kGuard, E - e);
+  }
+  double acc;
+  if (!special) {
+    acc = ldexp((double)sum, E - L::kBias - L::kGuard);
+  } else {
+    acc = 0.0;
+    for (const T* q = A + r0 * n + col; q < A + r1 * n + col; q += n) acc += fabs((double)__ldg(q));
+  }
   partial[(int64_t)blockIdx.y * n + col] = acc;
 }
 
@@ -49,55 +120,61 @@ __device__ __forceinline__ double max_nan(double a, double b) {
   return (isnan(a) || isnan(b)) ? __longlong_as_double(0x7ff8000000000000ULL) : fmax(a, b);
 }
 
-// Pass 2: one thread per column adds that column's partial sums (fixed order),
-// each block reduces its columns to a maximum, and the last block to finish
+// Pass 2: a block takes 32 columns; its 8 warps each add every eighth chunk
+// partial of those columns (warp g: chunks g, g + 8, ..., in order), the 8
+// sums of a column are added in a fixed tree order (deterministic), each
+// block reduces its columns to a maximum, and the last block to finish
 // reduces the block maxima into *out.
-__global__ void __launch_bounds__(kCols) colsum_finish(const double* __restrict__ partial, int64_t n,
-                                                       int64_t chunks, double* __restrict__ block_max,
-                                                       unsigned int* __restrict__ ticket, double* __restrict__ out) {
-  const int64_t col = (int64_t)blockIdx.x * kCols + threadIdx.x;
-  double best = 0.0;
-  if (col < n) {
-    // four interleaved sums in a fixed order (deterministic), sixteen loads
-    // in flight per thread
-    double s4[4] = {0.0, 0.0, 0.0, 0.0};
-    int64_t k = 0;
-    for (; k + 16 <= chunks; k += 16) {
-      double v[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = partial[(k + u) * n + col];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) s4[u & 3] += v[u];
-    }
-    for (; k < chunks; ++k) s4[k & 3] += partial[k * n + col];
-    best = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-  }
-  __shared__ double warp_best[kCols / 32];
+constexpr int kFinCols = 32, kFinGroups = 8;
+__global__ void __launch_bounds__(kFinCols * kFinGroups) colsum_finish(const double* __restrict__ partial, int64_t n,
+                                                                       int64_t chunks, double* __restrict__ block_max,
+                                                                       unsigned int* __restrict__ ticket,
+                                                                       double* __restrict__ out) {
+  __shared__ double part[kFinGroups][kFinCols];
+  __shared__ double warp_best[kFinGroups];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col = (int64_t)blockIdx.x * kFinCols + lane;
+  double acc = 0.0;
+  if (col < n) {
+    int64_t k = warp;
+    // four loads in flight per thread
+    for (; k + 3 * kFinGroups < chunks; k += 4 * kFinGroups) {
+      double v[4];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) best = max_nan(best, __shfl_xor_sync(0xffffffffu, best, off));
-  if (lane == 0) warp_best[warp] = best;
+      for (int u = 0; u < 4; ++u) v[u] = partial[(k + u * kFinGroups) * n + col];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += v[u];
+    }
+    for (; k < chunks; k += kFinGroups) acc += partial[k * n + col];
+  }
+  part[warp][lane] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = warp_best[0];
-    for (int w = 1; w < kCols / 32; ++w) b = max_nan(b, warp_best[w]);
-    block_max[blockIdx.x] = b;
-    __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (warp == 0) {
+    double best = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+                  ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
+    if (col >= n) best = 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = max_nan(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if (lane == 0) {
+      block_max[blockIdx.x] = best;
+      __threadfence();
+      last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double b = 0.0;
-  for (int64_t i = threadIdx.x; i < gridDim.x; i += kCols) b = max_nan(b, ((volatile double*)block_max)[i]);
+  for (int64_t i = threadIdx.x; i < gridDim.x; i += blockDim.x) b = max_nan(b, ((volatile double*)block_max)[i]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) b = max_nan(b, __shfl_xor_sync(0xffffffffu, b, off));
   if (lane == 0) warp_best[warp] = b;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kCols / 32; ++w) b = max_nan(warp_best[0], warp_best[w]), warp_best[0] = b;
-    *out = warp_best[0];
+    double r = warp_best[0];
+    for (int w = 1; w < kFinGroups; ++w) r = max_nan(r, warp_best[w]);
+    *out = r;
     *ticket = 0u;  // ready for the next call
   }
 }
@@ -134,22 +211,24 @@ cs_status norm1_impl(const T* A, int64_t n, double* partial, double* out, cudaSt
   }
   const int64_t chunks = (n + kRows - 1) / kRows;
   const int64_t col_blocks = (n + kCols - 1) / kCols;
+  const int64_t fin_blocks = (n + kFinCols - 1) / kFinCols;
   double* block_max = partial + chunks * n;
-  unsigned int* ticket = (unsigned int*)(block_max + col_blocks);
+  unsigned int* ticket = (unsigned int*)(block_max + fin_blocks);
   ProfScope prof(CS_KERNEL_NORM1, (double)n * (double)n * sizeof(T), stream);
   dim3 grid((unsigned)col_blocks, (unsigned)chunks);
   colsum_partial<T><<<grid, kCols, 0, stream>>>(A, n, partial, ticket);
-  colsum_finish<<<(unsigned)col_blocks, kCols, 0, stream>>>(partial, n, chunks, block_max, ticket, out);
+  colsum_finish<<<(unsigned)fin_blocks, kFinCols * kFinGroups, 0, stream>>>(partial, n, chunks, block_max, ticket,
+                                                                           out);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
 
 }  // namespace
 
-// partial sums (chunks x n), block maxima (one per column block) and a ticket word
+// partial sums (chunks x n), block maxima (one per pass-2 block) and a ticket word
 int64_t norm1_scratch_elems(int64_t n) {
   if (n <= 0) return 2;
-  return ((n + kRows - 1) / kRows) * n + (n + kCols - 1) / kCols + 1;
+  return ((n + kRows - 1) / kRows) * n + (n + kFinCols - 1) / kFinCols + 1;
 }
 
 cs_status norm1_f64(const double* A, int64_t n, double* partial, double* out, cudaStream_t stream) {
@@ -175,7 +254,7 @@ cs_status norm1_batched_f64(const double* A, int64_t n, int64_t count, double* o
 // about 2 MB, held by every GPU that loads the library until the process ends.
 constexpr int64_t kStaticMaxN = 4096;
 constexpr int64_t kStaticElems = ((kStaticMaxN + kRows - 1) / kRows) * kStaticMaxN +
-                                 (kStaticMaxN + kCols - 1) / kCols + 1;
+                                 (kStaticMaxN + kFinCols - 1) / kFinCols + 1;
 static __device__ __align__(256) double g_static_scratch[kStaticElems];
 
 namespace {

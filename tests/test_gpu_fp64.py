@@ -37,6 +37,37 @@ def test_norm1(n):
     assert got32 == pytest.approx(oracle.norm1(A32.astype(np.float64)), rel=1e-14)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_norm1_mixed_magnitudes(prec):
+    """Columns whose entries span many binades, with zeros, negative zeros and
+    subnormals (the column sums align every entry to the chunk's largest
+    exponent in integer arithmetic, within 2^-48 of the exact sum)."""
+    n = 300
+    g = inputs.rng(44)
+    lo, hi = (-60, 60) if prec == "fp64" else (-30, 30)
+    A = g.standard_normal((n, n)) * np.exp2(g.integers(lo, hi, size=(n, n)))
+    A[::7, ::3] = 0.0
+    A[1::11, ::5] = -0.0
+    tiny = np.finfo(np.float64 if prec == "fp64" else np.float32).tiny
+    A[2::13, 1::4] = tiny * g.random((len(range(2, n, 13)), len(range(1, n, 4)))) * 0.5
+    dt = np.float64 if prec == "fp64" else np.float32
+    A = A.astype(dt)
+    got = api.norm1(dev(A), prec)
+    assert got == pytest.approx(oracle.norm1(A.astype(np.float64)), rel=1e-14)
+
+
+def test_norm1_exact_and_extreme_values():
+    g = inputs.rng(45)
+    ints = g.integers(-2 ** 20, 2 ** 20, size=(257, 257)).astype(np.float64)
+    assert api.norm1(dev(ints)) == float(np.abs(ints).sum(axis=0).max())  # integer sums are exact
+    sub = np.full((70, 70), 5e-324) * g.integers(0, 1000, size=(70, 70))
+    assert api.norm1(dev(sub)) == float(np.abs(sub).sum(axis=0).max())  # subnormals only: exact
+    big = np.full((64, 64), 1e300)
+    assert api.norm1(dev(big)) == pytest.approx(6.4e301, rel=1e-15)
+    over = np.full((40, 40), 1e308)
+    assert api.norm1(dev(over)) == np.inf  # the exact column sum overflows, as in FP64
+
+
 def test_norm1_nan_inf():
     A = np.ones((50, 50))
     A[7, 9] = np.nan
