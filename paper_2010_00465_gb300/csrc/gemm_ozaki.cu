@@ -100,6 +100,11 @@ constexpr int kCols = BN / 2;          // columns per epilogue warp
 constexpr int kABytes = BM * BK * 2;   // one A slice of a stage
 constexpr int kBBytes = BN * BK * 2;   // one B slice of a stage
 constexpr int kGroupM = 8;             // M tiles per raster group
+// TMA boxes of 256 rows: a tile's slices lie next to each other in global
+// memory (and in a stage), so one box carries two A slices (2 x 128 rows) or
+// four B slices (4 x 64 rows): 6 loads per stage instead of 16 for S = 8.
+constexpr int kBoxRows = 256;
+constexpr int kBoxBytes = kBoxRows * BK * 2;
 constexpr int kStageRows = 32;          // rows of the tile staged per epilogue round
 constexpr int kLd = 2 * kCols + 1;      // staging row pitch (doubles)
 // Per slice count S: all S slices of A and B^T of one k-block form a stage,
@@ -239,9 +244,10 @@ __global__ void col_exp_kernel(const double* __restrict__ Y, int64_t ld, const u
   }
 }
 
-// Left operand: out[b][s][r][k] (row-major, K contiguous) for r < rows_pad,
-// k < ldk, matrix b = blockIdx.y of a batch; rows >= rows and k >= cols are
-// zero.
+// Left operand: out[b][t][s][i][k] for row r = t BM + i < rows_pad (tile t
+// of BM rows, its S slices next to each other so that one TMA box carries
+// several), k < ldk (K contiguous), matrix b = blockIdx.y of a batch; rows
+// >= rows and k >= cols are zero.
 template <int S>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
                                                          int64_t ld, const int* __restrict__ ex,
@@ -256,14 +262,17 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     __nv_bfloat16 q[S];
     const double x = (r < rows && k < cols && k != r % cols) ? X[r * ld + k] : 0.0;
     cut(x, r < rows ? ex[r] : 0, q);
+    const int64_t t = r / BM, ri = r - t * BM;
+    __nv_bfloat16* o = out + ((t * S) * BM + ri) * ldk + k;
 #pragma unroll
-    for (int s = 0; s < S; ++s) out[s * plane + i] = q[s];
+    for (int s = 0; s < S; ++s) o[(int64_t)s * BM * ldk] = q[s];
   }
 }
 
-// Right operand Y (rows = K, cols = N, row-major): out[s][c][k], the
-// transposed slices (K contiguous) for c < cols_pad, k < ldk, through a
-// 32 x 32 shared-memory tile per slice.
+// Right operand Y (rows = K, cols = N, row-major): out[t][s][j][k] for column
+// c = t BN + j < cols_pad, the transposed slices (K contiguous, the S slices
+// of a BN-column tile next to each other), k < ldk, through a 32 x 32
+// shared-memory tile per slice.
 template <int S>
 __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ Y, int64_t rows, int64_t cols,
                                                          int64_t ld, const int* __restrict__ ex,
@@ -284,12 +293,13 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restric
     for (int s = 0; s < S; ++s) tile[s][j][tx] = q[s];
   }
   __syncthreads();
-  const int64_t plane = cols_pad * ldk;
   for (int j = ty; j < 32; j += 8) {
     const int64_t c = c0 + j, k = k0 + tx;
     if (c >= cols_pad || k >= ldk) continue;
+    const int64_t t = c / BN, ci = c - t * BN;
+    __nv_bfloat16* o = out + ((t * S) * BN + ci) * ldk + k;
 #pragma unroll
-    for (int s = 0; s < S; ++s) out[s * plane + c * ldk + k] = tile[s][tx][j];
+    for (int s = 0; s < S; ++s) o[(int64_t)s * BN * ldk] = tile[s][tx][j];
   }
 }
 
@@ -388,10 +398,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           uint8_t* base = smem + st * kStageBytes;
           mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
-          for (int s = 0; s < S; ++s) {
-            tma_load_2d(base + s * kABytes, &mA, &full_bar[st], kb * BK, (bat * S + s) * Mpad + m0);
-            tma_load_2d(base + S * kABytes + s * kBBytes, &mB, &full_bar[st], kb * BK, (bat * S + s) * Npad + n0);
-          }
+          // the S slices of tile (m0, n0): rows a_row0 .. + S BM of the A
+          // slices, b_row0 .. + S BN of the B slices
+          const int a_row0 = (bat * nM + m0 / BM) * S * BM, b_row0 = (bat * nN + n0 / BN) * S * BN;
+#pragma unroll
+          for (int h = 0; h < S * BM / kBoxRows; ++h)
+            tma_load_2d(base + h * kBoxBytes, &mA, &full_bar[st], kb * BK, a_row0 + h * kBoxRows);
+#pragma unroll
+          for (int h = 0; h < S * BN / kBoxRows; ++h)
+            tma_load_2d(base + S * kABytes + h * kBoxBytes, &mB, &full_bar[st], kb * BK, b_row0 + h * kBoxRows);
           kb_issued = g + 1;
         }
       }
@@ -711,8 +726,9 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   }
   ProfScope prof(CS_KERNEL_GEMM_EMU, 2.0 * (double)batch * (double)M * (double)N * (double)K, stream);
   CUtensorMap mA, mB;
-  CS_CHECK(make_map(&mA, a_sl, batch * S * d.Mpad, d.ldk, d.ldk, BM));
-  CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, BN));
+  static_assert(S * BM % kBoxRows == 0 && S * BN % kBoxRows == 0, "whole boxes of slices");
+  CS_CHECK(make_map(&mA, a_sl, batch * S * d.Mpad, d.ldk, d.ldk, kBoxRows));
+  CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, kBoxRows));
   static bool attr_set = false;
   if (!attr_set) {
     CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
