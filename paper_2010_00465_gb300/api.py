@@ -6,6 +6,7 @@ fallback: without the built library or a GPU these calls raise.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import torch
@@ -73,14 +74,26 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
            workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
     """cos(A), sin(A) of a square matrix.
 
-    ``prec``: "fp64", "fp32" or "split_tf32" (default from A's dtype).  A CPU
-    tensor is copied to the current device and the results are copied back.
-    ``m``/``s`` force the family 2m and the number of double-angle steps.
+    ``prec``: "fp64", "fp32", "split_tf32", "fp64_emu", "split_emu" or
+    "split_bf16" (default from A's dtype).  A CPU tensor is copied to the
+    current device and the results are copied back: into ``out`` = (C, S) if
+    given as CPU tensors (pinned ones are filled by asynchronous copies on the
+    call's stream, which is synchronised before returning), else into new CPU
+    tensors.  For a device A, ``out`` holds device tensors.  ``m``/``s`` force
+    the family 2m and the number of double-angle steps.
     """
     p = _prec(prec, A)
     host = not A.is_cuda
+    host_out = None
     if host:
-        A = A.to("cuda", non_blocking=True)
+        if out is not None:
+            host_out = out
+            for X in host_out:
+                if X.is_cuda or X.shape != A.shape or X.dtype != A.dtype or not X.is_contiguous():
+                    raise ValueError("host outputs must be contiguous CPU tensors shaped and typed like A")
+            out = None
+        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+            A = A.to("cuda", non_blocking=True)
     A = A.contiguous()
     n = _check_matrix(A, p)
     if out is None:
@@ -99,8 +112,16 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
                           workspace.numel() * workspace.element_size(), fm, fs, ctypes.byref(info),
                           _stream_ptr(stream)))
     if host:
-        C = C.cpu()
-        S = S.cpu()
+        if host_out is not None:
+            st = stream if stream is not None else torch.cuda.current_stream()
+            with torch.cuda.stream(st):
+                host_out[0].copy_(C, non_blocking=True)
+                host_out[1].copy_(S, non_blocking=True)
+            st.synchronize()
+            C, S = host_out
+        else:
+            C = C.cpu()
+            S = S.cpu()
     if return_info:
         return C, S, info.as_dict()
     return C, S

@@ -243,3 +243,25 @@ def test_full_size_symmetric_eigh():
     Sr = (V * torch.sin(w)) @ V.T
     assert float((C - Cr).norm() / Cr.norm()) <= TOL64
     assert float((S - Sr).norm() / Sr.norm()) <= TOL64
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_tensors_round_trip(pinned):
+    """A CPU input is copied in, the results come back into the caller's CPU
+    outputs (pinned: asynchronous copies on the call's stream, then a
+    synchronisation), equal to the device call's results."""
+    A = inputs.matrix(300, "normal", 8.0, index=46)
+    C_dev, S_dev = api.cossin(dev(A), "fp64")
+    host_A = torch.from_numpy(A)
+    if pinned:
+        host_A = host_A.pin_memory()
+    out = (torch.empty(300, 300, dtype=torch.float64, pin_memory=pinned),
+           torch.empty(300, 300, dtype=torch.float64, pin_memory=pinned))
+    stream = torch.cuda.Stream()
+    C, S = api.cossin(host_A, "fp64", out=out, stream=stream)
+    assert C.data_ptr() == out[0].data_ptr() and S.data_ptr() == out[1].data_ptr()
+    assert torch.equal(C, C_dev.cpu()) and torch.equal(S, S_dev.cpu())
+    C2, S2 = api.cossin(torch.from_numpy(A), "fp64")
+    assert torch.equal(C2, C) and torch.equal(S2, S)
+    with pytest.raises(ValueError):
+        api.cossin(host_A, "fp64", out=(torch.empty(3, 3, dtype=torch.float64), out[1]))
