@@ -92,8 +92,10 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
                 if X.is_cuda or X.shape != A.shape or X.dtype != A.dtype or not X.is_contiguous():
                     raise ValueError("host outputs must be contiguous CPU tensors shaped and typed like A")
             out = None
+        # on the call's stream; asynchronous only from pinned memory (a copy
+        # from pageable memory blocks until the data is on the device)
         with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
-            A = A.to("cuda", non_blocking=True)
+            A = A.to("cuda", non_blocking=A.is_pinned())
     A = A.contiguous()
     n = _check_matrix(A, p)
     if out is None:
@@ -115,13 +117,14 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
         if host_out is not None:
             st = stream if stream is not None else torch.cuda.current_stream()
             with torch.cuda.stream(st):
-                host_out[0].copy_(C, non_blocking=True)
-                host_out[1].copy_(S, non_blocking=True)
+                host_out[0].copy_(C, non_blocking=host_out[0].is_pinned())
+                host_out[1].copy_(S, non_blocking=host_out[1].is_pinned())
             st.synchronize()
             C, S = host_out
         else:
-            C = C.cpu()
-            S = S.cpu()
+            with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+                C = C.cpu()
+                S = S.cpu()
     if return_info:
         return C, S, info.as_dict()
     return C, S
@@ -144,8 +147,10 @@ def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None
     """
     p = _prec(prec, A)
     host = not A.is_cuda
+    ctx = (lambda: torch.cuda.stream(stream)) if stream is not None else contextlib.nullcontext
     if host:
-        A = A.to("cuda", non_blocking=True)
+        with ctx():
+            A = A.to("cuda", non_blocking=A.is_pinned())
     A = A.contiguous()
     n = _check_matrix(A, p)
     if out is None:
@@ -164,8 +169,9 @@ def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None
                           workspace.numel() * workspace.element_size(), ff, fs, ctypes.byref(info),
                           _stream_ptr(stream)))
     if host:
-        C = C.cpu()
-        S = S.cpu()
+        with ctx():
+            C = C.cpu()
+            S = S.cpu()
     if return_info:
         return C, S, info.as_dict()
     return C, S
