@@ -6,8 +6,9 @@ fallback: without the built library or a GPU these calls raise.
 """
 from __future__ import annotations
 
-import contextlib
 import ctypes
+import functools
+import inspect
 
 import torch
 
@@ -35,6 +36,23 @@ def _stream_ptr(stream) -> int:
     return int(s.cuda_stream)
 
 
+def _on_stream(fn):
+    """Run the call with its ``stream`` argument (if given) as PyTorch's
+    current stream, so that the outputs and workspaces it allocates come from
+    that stream's pool: memory freed by work still pending on another stream
+    is never handed to a launch on this one."""
+    sig = inspect.signature(fn)
+
+    @functools.wraps(fn)
+    def wrapper(*args, **kwargs):
+        stream = sig.bind_partial(*args, **kwargs).arguments.get("stream")
+        if stream is None:
+            return fn(*args, **kwargs)
+        with torch.cuda.stream(stream):
+            return fn(*args, **kwargs)
+    return wrapper
+
+
 def _check_matrix(A: torch.Tensor, p: int) -> int:
     if A.dim() != 2 or A.shape[0] != A.shape[1]:
         raise ValueError("A must be square, got %r" % (tuple(A.shape),))
@@ -53,6 +71,7 @@ def workspace_size(n: int, prec="fp64") -> int:
     return int(out.value)
 
 
+@_on_stream
 def norm1(A: torch.Tensor, prec=None, stream=None) -> float:
     """||A||_1 computed on the device (FP64 accumulation)."""
     p = _prec(prec, A)
@@ -70,6 +89,7 @@ def select(norm: float, table: int):
     return m.value, s.value
 
 
+@_on_stream
 def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = None,
            workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
     """cos(A), sin(A) of a square matrix.
@@ -94,8 +114,7 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
             out = None
         # on the call's stream; asynchronous only from pinned memory (a copy
         # from pageable memory blocks until the data is on the device)
-        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
-            A = A.to("cuda", non_blocking=A.is_pinned())
+        A = A.to("cuda", non_blocking=A.is_pinned())
     A = A.contiguous()
     n = _check_matrix(A, p)
     if out is None:
@@ -115,16 +134,13 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
                           _stream_ptr(stream)))
     if host:
         if host_out is not None:
-            st = stream if stream is not None else torch.cuda.current_stream()
-            with torch.cuda.stream(st):
-                host_out[0].copy_(C, non_blocking=host_out[0].is_pinned())
-                host_out[1].copy_(S, non_blocking=host_out[1].is_pinned())
-            st.synchronize()
+            host_out[0].copy_(C, non_blocking=host_out[0].is_pinned())
+            host_out[1].copy_(S, non_blocking=host_out[1].is_pinned())
+            torch.cuda.current_stream().synchronize()
             C, S = host_out
         else:
-            with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
-                C = C.cpu()
-                S = S.cpu()
+            C = C.cpu()
+            S = S.cpu()
     if return_info:
         return C, S, info.as_dict()
     return C, S
@@ -138,6 +154,7 @@ def cs_select(normB: float, table: int):
     return f.value, sg.value
 
 
+@_on_stream
 def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None, sigma: int | None = None,
               workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
     """c(t^2 A) = cos(sqrt(t^2 A)) and s(t, A) = A^(-1/2) sin(sqrt(t^2 A)) (Sec. 2.2).
@@ -147,10 +164,8 @@ def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None
     """
     p = _prec(prec, A)
     host = not A.is_cuda
-    ctx = (lambda: torch.cuda.stream(stream)) if stream is not None else contextlib.nullcontext
     if host:
-        with ctx():
-            A = A.to("cuda", non_blocking=A.is_pinned())
+        A = A.to("cuda", non_blocking=A.is_pinned())
     A = A.contiguous()
     n = _check_matrix(A, p)
     if out is None:
@@ -169,14 +184,14 @@ def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None
                           workspace.numel() * workspace.element_size(), ff, fs, ctypes.byref(info),
                           _stream_ptr(stream)))
     if host:
-        with ctx():
-            C = C.cpu()
-            S = S.cpu()
+        C = C.cpu()
+        S = S.cpu()
     if return_info:
         return C, S, info.as_dict()
     return C, S
 
 
+@_on_stream
 def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Tensor:
     """P = X Y on the library's product kernel for ``prec``."""
     p = _prec(prec, X)
@@ -189,6 +204,7 @@ def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Te
     return P
 
 
+@_on_stream
 def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m: int | None = None,
                     s: int | None = None, want_forward: bool = False, stream=None, return_info: bool = False,
                     prec: str = "fp64"):
@@ -238,6 +254,7 @@ def unitary_workspace_size(n: int, prec="fp64") -> int:
     return out.value
 
 
+@_on_stream
 def unitary(A: torch.Tensor, t: float, prec=None, *, m: int | None = None, s: int | None = None,
             workspace: torch.Tensor | None = None, stream=None, return_info: bool = False):
     """U = exp(-i t A) = cos(tA) - i sin(tA) of a real square matrix (complex128
@@ -258,6 +275,7 @@ def unitary(A: torch.Tensor, t: float, prec=None, *, m: int | None = None, s: in
     return (U, info.as_dict()) if return_info else U
 
 
+@_on_stream
 def unitary_backward(A: torch.Tensor, t: float, G: torch.Tensor, *, m: int | None = None, s: int | None = None,
                      want_forward: bool = False, stream=None, return_info: bool = False):
     """d/dA of Re sum(conj(G) * exp(-i t A)) (FP64; A real n x n or [count, n, n],
@@ -355,6 +373,7 @@ class BatchedPlan:
     inputs; results land in ``self.C`` / ``self.S``; ``infos()`` and
     ``status()`` read the per-matrix record of the last launch."""
 
+    @_on_stream
     def __init__(self, mats, autotune: bool = True, stream=None, out=None):
         import numpy as np
         self.A = list(mats)
@@ -413,6 +432,7 @@ class BatchedPlan:
             pass
 
 
+@_on_stream
 def cossin_batched(mats, stream=None):
     """One-shot batched cos/sin (no graph); returns (C list, S list, infos, status)."""
     import numpy as np
