@@ -237,8 +237,8 @@ cs_status cossin_backward_ex(int64_t count, int64_t n, const double* A_dev, cons
  * (Tables 1-2) and t is folded into the first and last products, so no
  * scaled copy of A is made.
  *   U_dev: n x n complex, interleaved (re, im) pairs of the precision's real
- *          type (complex128 for CS_FP64 and CS_SPLIT_TF32, complex64 for
- *          CS_FP32); must not overlap A.
+ *          type (complex64 for CS_FP32, complex128 for every other prec);
+ *          must not overlap A.
  *   ws_dev: at least cossin_unitary_workspace_size bytes, 256-byte aligned,
  *          or NULL to allocate on `stream`.
  * force_m / force_s and info as cossin_ex (info->norm1 = ||tA||_1).

@@ -257,8 +257,8 @@ def unitary_workspace_size(n: int, prec="fp64") -> int:
 @_on_stream
 def unitary(A: torch.Tensor, t: float, prec=None, *, m: int | None = None, s: int | None = None,
             workspace: torch.Tensor | None = None, stream=None, return_info: bool = False):
-    """U = exp(-i t A) = cos(tA) - i sin(tA) of a real square matrix (complex128
-    for "fp64"/"split_tf32", complex64 for "fp32")."""
+    """U = exp(-i t A) = cos(tA) - i sin(tA) of a real square matrix (complex64
+    for "fp32", complex128 for every other precision)."""
     p = _prec(prec, A)
     A = A.contiguous()
     n = _check_matrix(A, p)

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kCols) colsum_partial(const T* __restrict__ A,
     acc = ldexp((double)sum, E - L::kBias - L::kGuard);
   } else {
     acc = 0.0;
-    for (const T* q = A + r0 * n + col; q < A + r1 * n + col; q += n) acc += fabs((double)__ldg(q));
+    for (int64_t rr = r0; rr < r1; ++rr) acc += fabs((double)__ldg(A + rr * n + col));
   }
   partial[(int64_t)blockIdx.y * n + col] = acc;
 }
