@@ -44,14 +44,16 @@
 // The same kernel with S = 4 is the BF16 multi-term product of the
 // split-precision form: 29 bits of each row / column maximum, 10 slice
 // products (levels 0..3, all summed exactly), at most 2^-25 K max|X_i.|
-// max|Y_.j| per entry; its level accumulators take 256 TMEM columns, so two
-// sets alternate between chunks and the MMAs of one chunk overlap the
-// epilogue's reading of the previous one.
+// max|Y_.j| per entry; its stages hold 64-wide k-blocks, and its level
+// accumulators take 256 TMEM columns, so two sets alternate between chunks
+// and the MMAs of one chunk overlap the epilogue's reading of the previous
+// one.
 //
 // One CTA computes a 128 x 64 tile (S = 8):
-//   warp 0     TMA producer: all S slices of A (128 x 32) and of B^T (64 x 32)
-//              for one 32-wide k-block per stage, 64-byte swizzle, 192 KB of
-//              stages (2 for S = 8, 4 for S = 4);
+//   warp 0     TMA producer: all S slices of A (128 x BK) and of B^T
+//              (64 x BK) for one k-block per stage, 2 stages of 96 KB (BK = 32
+//              with 64-byte swizzle for S = 8, BK = 64 with 128-byte swizzle
+//              for S = 4);
 //   warp 1     allocates 512 TMEM columns (8 level accumulators of 64
 //              columns; two sets of 4 for S = 4) and issues the MMAs
 //              (cta_group::1, M = 128, K = 16):
@@ -85,32 +87,27 @@ using namespace ptx;
 
 constexpr int BM = 128;
 constexpr int BN = 64;
-#ifndef COSSIN_OZAKI_BK
-#define COSSIN_OZAKI_BK 32
-#endif
-// k per pipeline stage: 32 bf16 = 64 bytes (64-byte swizzle, 2 stages) or
-// 16 = 32 bytes (32-byte swizzle, 4 stages); the same 192 KB of slices in
-// flight.  The 32-wide stage measured 5 % faster (fewer barriers and commits).
-constexpr int BK = COSSIN_OZAKI_BK;
-constexpr int kSwizzleBytes = BK * 2;  // one swizzle row = one stage row
-constexpr int kChunkKb = 512 / BK;     // k-blocks per 512-k accumulator chunk
+// k per pipeline stage (BK bf16 = one swizzle row of 2 BK bytes): 32 for
+// eight slices (64-byte swizzle, 2 stages of 96 KB; a 16-wide stage with
+// 4 stages measured 5 % slower), 64 for four slices (128-byte swizzle,
+// 2 stages of 96 KB).
+__host__ __device__ constexpr int stage_k(int S) { return S == kOzakiSlicesSplit ? 64 : 32; }
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kCols = BN / 2;          // columns per epilogue warp
-constexpr int kABytes = BM * BK * 2;   // one A slice of a stage
-constexpr int kBBytes = BN * BK * 2;   // one B slice of a stage
 constexpr int kGroupM = 8;             // M tiles per raster group
 // TMA boxes of 256 rows: a tile's slices lie next to each other in global
 // memory (and in a stage), so one box carries two A slices (2 x 128 rows) or
 // four B slices (4 x 64 rows): 6 loads per stage instead of 16 for S = 8.
 constexpr int kBoxRows = 256;
-constexpr int kBoxBytes = kBoxRows * BK * 2;
 constexpr int kStageRows = 32;          // rows of the tile staged per epilogue round
 constexpr int kLd = 2 * kCols + 1;      // staging row pitch (doubles)
 // Per slice count S: all S slices of A and B^T of one k-block form a stage,
-// 192 KB of stages are in flight (2 stages for S = 8, 4 for S = 4), and the
-// S level accumulators of BN columns fill S BN TMEM columns.
-__host__ __device__ constexpr int stage_bytes(int S) { return S * (kABytes + kBBytes); }
+// 192 KB of stages are in flight, and the S level accumulators of BN columns
+// fill S BN TMEM columns.
+__host__ __device__ constexpr int a_slice_bytes(int S) { return BM * stage_k(S) * 2; }  // one A slice of a stage
+__host__ __device__ constexpr int b_slice_bytes(int S) { return BN * stage_k(S) * 2; }  // one B slice of a stage
+__host__ __device__ constexpr int stage_bytes(int S) { return S * (a_slice_bytes(S) + b_slice_bytes(S)); }
 __host__ __device__ constexpr int num_stages(int S) { return (192 * 1024) / stage_bytes(S); }
 __host__ __device__ constexpr int smem_bytes(int S) {
   return num_stages(S) * stage_bytes(S) + kStageRows * kLd * 8 + 1024;  // stages + epilogue staging
@@ -323,6 +320,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse,
                  int batch) {
   constexpr int kAcc = S;  // one accumulator of BN columns per level p + q < S
+  constexpr int BK = stage_k(S);
+  constexpr int kSwizzleBytes = BK * 2;  // one swizzle row = one stage row
+  constexpr int kChunkKb = 512 / BK;     // k-blocks per 512-k accumulator chunk
+  constexpr int kABytes = a_slice_bytes(S);
+  constexpr int kBBytes = b_slice_bytes(S);
+  constexpr int kBoxBytes = kBoxRows * BK * 2;
   constexpr int kStageBytes = stage_bytes(S);
   constexpr int kStages = num_stages(S);
   // Two sets of level accumulators when they fit in the 512 TMEM columns
@@ -419,7 +422,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // is at a compile-time offset from the stage base, so each MMA costs
       // two integer adds to issue.
       constexpr uint32_t kDescHi =
-          ((uint32_t)(8 * kSwizzleBytes) >> 4) | (1u << 14) | ((kSwizzleBytes == 32 ? 6u : 4u) << 29);
+          ((uint32_t)(8 * kSwizzleBytes) >> 4) | (1u << 14) |
+          ((kSwizzleBytes == 32 ? 6u : kSwizzleBytes == 64 ? 4u : 2u) << 29);
       int g = 0;   // k-blocks consumed so far, over all tiles
       int cg = 0;  // chunks committed so far, over all tiles
       for (int u = blockIdx.x; u < total && !abort_flag; u += gridDim.x) {
@@ -654,17 +658,18 @@ EncodeTiledFn encode_fn() {
 }
 
 // Row-major BF16 matrix [rows][cols] (leading dimension ld elements), box of
-// 32 columns x box_rows rows, 64-byte swizzle.
-cs_status make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// box_k columns x box_rows rows, swizzle of 2 box_k bytes (64 or 128).
+cs_status make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_k,
+                   int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return fail(CS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
   if (((uintptr_t)base & 15) || (ld * 2) % 16) return fail(CS_EINVAL, "TMA operand not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, kSwizzleBytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(CS_ECUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
@@ -727,8 +732,8 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   ProfScope prof(CS_KERNEL_GEMM_EMU, 2.0 * (double)batch * (double)M * (double)N * (double)K, stream);
   CUtensorMap mA, mB;
   static_assert(S * BM % kBoxRows == 0 && S * BN % kBoxRows == 0, "whole boxes of slices");
-  CS_CHECK(make_map(&mA, a_sl, batch * S * d.Mpad, d.ldk, d.ldk, kBoxRows));
-  CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, kBoxRows));
+  CS_CHECK(make_map(&mA, a_sl, batch * S * d.Mpad, d.ldk, d.ldk, stage_k(S), kBoxRows));
+  CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, stage_k(S), kBoxRows));
   static bool attr_set = false;
   if (!attr_set) {
     CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
