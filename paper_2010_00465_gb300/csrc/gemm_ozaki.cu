@@ -734,11 +734,8 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   static_assert(S * BM % kBoxRows == 0 && S * BN % kBoxRows == 0, "whole boxes of slices");
   CS_CHECK(make_map(&mA, a_sl, batch * S * d.Mpad, d.ldk, d.ldk, stage_k(S), kBoxRows));
   CS_CHECK(make_map(&mB, b_sl, batch * S * d.Npad, d.ldk, d.ldk, stage_k(S), kBoxRows));
-  static bool attr_set = false;
-  if (!attr_set) {
-    CS_CUDA_CHECK(cudaFuncSetAttribute(ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> smem_set{0};
+  CS_CHECK(smem_limit_once(ozaki_kernel<S>, kSmem, smem_set));
   const int64_t tiles = (d.Npad / BN) * (d.Mpad / BM) * batch;
   if (tiles > INT32_MAX) return fail(CS_EINVAL, "gemm_f64_emu: grid too large");
   int sms = 0, dev = 0;

@@ -439,11 +439,8 @@ cs_status launch(const TcOperand& X, const TcOperand& YT, int M, int N, int K, i
   CS_CHECK(make_map(&mXl, X.lo, M, K, X.ld, BM));
   CS_CHECK(make_map(&mYh, YT.hi, N, K, YT.ld, BN));
   CS_CHECK(make_map(&mYl, YT.lo, N, K, YT.ld, BN));
-  static bool attr_set = false;
-  if (!attr_set) {
-    CS_CUDA_CHECK(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> smem_set{0};
+  CS_CHECK(smem_limit_once(gemm_tf32_kernel, kSmem, smem_set));
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   gemm_tf32_kernel<<<grid, kThreads, kSmem, stream>>>(mXh, mXl, mYh, mYl, M, N, K, ldo, epi, err);
   CS_CUDA_CHECK(cudaGetLastError());

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "cossin.h"
@@ -26,6 +27,20 @@ cs_status cuda_fail(cudaError_t e, const char* what);
     cs_status st_ = (expr);                  \
     if (st_ != CS_OK) return st_;            \
   } while (0)
+
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` once per device
+// (the attribute belongs to the device's context); `done` holds one bit per
+// device ordinal below 64, others are set on every call.
+template <typename Kernel>
+inline cs_status smem_limit_once(Kernel* kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  CS_CUDA_CHECK(cudaGetDevice(&dev));
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ULL << dev : 0ULL;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return CS_OK;
+  CS_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_acq_rel);
+  return CS_OK;
+}
 
 // --------------------------------------------------------------- epilogue ---
 // Every product P = X Y of the method is followed by linear combinations of P,
