@@ -283,6 +283,7 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
                         cs_info* infos_host, cudaStream_t st, bool emu) {
   if (count < 0 || n < 0 || n > kMaxN) return fail(CS_EINVAL, "count or n out of range");
+  if (n > 0 && count > (int64_t(1) << 46) / (n * n)) return fail(CS_EINVAL, "count * n^2 above 2^46 elements");
   if (emu && n > kOzakiMaxK) return fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
   if (!isfinite(scale)) return fail(CS_EINVAL, "t must be finite");
   if ((force_m == -1) != (force_s == -1)) return fail(CS_EINVAL, "force_m and force_s must both be -1 or both set");

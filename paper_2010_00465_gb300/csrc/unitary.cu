@@ -108,6 +108,7 @@ extern "C" cs_status cossin_unitary_backward(int64_t count, int64_t n, double t,
   using namespace cs;
   cudaStream_t st = (cudaStream_t)stream;
   if (count < 0 || n < 0 || n > kMaxN) return fail(CS_EINVAL, "count or n out of range");
+  if (n > 0 && count > (int64_t(1) << 46) / (n * n)) return fail(CS_EINVAL, "count * n^2 above 2^46 elements");
   if (!isfinite(t)) return fail(CS_EINVAL, "t must be finite");
   if (count == 0 || n == 0) return backward_impl(count, n, t, A, nullptr, nullptr, dA, nullptr, nullptr, force_m,
                                                  force_s, infos_host, st);

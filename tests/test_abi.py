@@ -120,6 +120,18 @@ def test_emulated_precisions_host_checks(L):
                                 nul) == _lib.CS_EINVAL
 
 
+def test_adjoint_sizes_that_would_overflow_are_refused(L):
+    """count * n^2 beyond 2^46 elements is refused before any device work
+    (the byte counts would wrap)."""
+    nul = ctypes.c_void_p(0)
+    p = ctypes.c_void_p(4096)
+    huge = 1 << 40
+    assert L.cossin_backward(huge, 4096, p, p, p, p, nul, nul, -1, -1, None, nul) == _lib.CS_EINVAL
+    assert b"2^46" in L.cossin_last_error()
+    assert L.cossin_unitary_backward(huge, 4096, 1.0, p, p, p, nul, -1, -1, None, nul) == _lib.CS_EINVAL
+    assert b"2^46" in L.cossin_last_error()
+
+
 def test_cs_and_unitary_argument_errors_before_any_gpu_work(L):
     nul = ctypes.c_void_p(0)
     info = _lib.CsInfo()
