@@ -450,11 +450,10 @@ cs_status launch(const TcOperand& X, const TcOperand& YT, int M, int N, int K, i
 }  // namespace
 
 cs_status gemm_tf32(const TcOperand& X, const TcOperand& YT, int64_t M, int64_t N, int64_t K, int64_t ldo,
-                    const TcEpilogue& epi, int* err, int bn, cudaStream_t stream) {
+                    const TcEpilogue& epi, int* err, cudaStream_t stream) {
   if (M <= 0 || N <= 0) return CS_OK;
   if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return fail(CS_EINVAL, "gemm_tf32: size too large");
   ProfScope prof(CS_KERNEL_GEMM_TF32, 2.0 * (double)M * (double)N * (double)K, stream);
-  (void)bn;
   return launch(X, YT, (int)M, (int)N, (int)K, (int)ldo, epi, err, stream);
 }
 

@@ -39,10 +39,10 @@ struct TcEpilogue {
 };
 
 // P = X (M x K) times Y (K x N), Y given transposed (YT: N x K), both K-major.
-// ldo: leading dimension of every epilogue matrix.  bn: 128 or 256 (tile width).
+// ldo: leading dimension of every epilogue matrix (128 x 128 output tiles).
 // *err (device int) is set to 1 if a bounded wait expired.
 cs_status gemm_tf32(const TcOperand& X, const TcOperand& YT, int64_t M, int64_t N, int64_t K, int64_t ldo,
-                    const TcEpilogue& epi, int* err, int bn, cudaStream_t stream);
+                    const TcEpilogue& epi, int* err, cudaStream_t stream);
 
 // (hi, lo) split of scale * (an n x n row-major matrix, FP32 or FP64 source,
 // leading dimension n) into padded (ld) hi/lo and, if hiT is non-null, the

@@ -19,16 +19,6 @@ struct TcSlot {
   float* loT = nullptr;
 };
 
-int tile_bn(int64_t n) {
-  static int forced = -1;
-  if (forced < 0) {
-    const char* e = getenv("COSSIN_TC_BN");
-    forced = e ? atoi(e) : 0;
-  }
-  if (forced == 128 || forced == 256) return forced;
-  return n >= 2048 ? 256 : 128;
-}
-
 // Is the matrix written into `slot` by step i read as a right operand later
 // (before it is overwritten)?  Right operands are fed transposed.
 bool needs_transpose(const std::vector<Step>& plan, size_t i, int slot, bool squaring_follows) {
@@ -56,7 +46,6 @@ cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, cha
   slot[SL_S] = {ping[0].hi + n * ld, ping[0].lo + n * ld, nullptr, nullptr};
   int* err = tc_error_word();
   if (!err) return fail(CS_ECUDA, "cannot resolve the device error word");
-  const int bn = tile_bn(n);
 
   // The input goes to SL_A, or scaled to W0 for the c(t^2 A), s(t, A) variant.
   const TcSlot& in = spec.scale_into_w0 ? slot[W(0)] : slot[SL_A];
@@ -94,7 +83,7 @@ cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, cha
     }
     const TcOperand X{slot[st.X].hi, slot[st.X].lo, ld};
     const TcOperand YT{slot[st.Y].hiT, slot[st.Y].loT, ld};
-    CS_CHECK(gemm_tf32(X, YT, n, n, n, ld, e, err, bn, stream));
+    CS_CHECK(gemm_tf32(X, YT, n, n, n, ld, e, err, stream));
   }
 
   if (prec == CS_FP32) {
@@ -116,7 +105,7 @@ cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, cha
       e.gamma[1] = 0.f;
       const TcOperand X{cur.hi, cur.lo, ld};
       const TcOperand YT{cur.hiT, cur.loT, ld};
-      CS_CHECK(gemm_tf32(X, YT, 2 * n, n, n, ld, e, err, bn, stream));
+      CS_CHECK(gemm_tf32(X, YT, 2 * n, n, n, ld, e, err, stream));
     }
     const TcSlot& fin = ping[s & 1];
     CS_CHECK(combine_f32(fin.hi, fin.lo, n, ld, (float*)C, stream));
@@ -158,7 +147,7 @@ cs_status matmul_tf32(const void* X, const void* Y, int64_t n, bool f64_io, void
     e.out_lo[0] = b[7];
     e.alpha[0] = 1.f;
     int* err = tc_error_word();
-    rc = err ? gemm_tf32(TcOperand{b[0], b[1], ld}, TcOperand{b[4], b[5], ld}, n, n, n, ld, e, err, tile_bn(n), stream)
+    rc = err ? gemm_tf32(TcOperand{b[0], b[1], ld}, TcOperand{b[4], b[5], ld}, n, n, n, ld, e, err, stream)
              : fail(CS_ECUDA, "cannot resolve the device error word");
   }
   if (rc == CS_OK)
