@@ -66,9 +66,6 @@ static_assert(3 * BM * BN * 4 <= kStages * kStageBytes, "epilogue tiles fit the 
 #ifndef COSSIN_TC_GROUP
 #define COSSIN_TC_GROUP 1
 #endif
-#ifndef COSSIN_TC_PASSES
-#define COSSIN_TC_PASSES 4
-#endif
 constexpr int kGroup = COSSIN_TC_GROUP;  // k-blocks per accumulator buffer before promotion
 constexpr uint32_t kTmemCols = 512;    // main buffer b at 128 b, corrections at 256, compensation at 384
 // Instruction descriptor: D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12),
@@ -184,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_tf32(d_main, ah, bh, kIdesc, j ? 1u : fresh_main);  // fresh every group
             mma_tf32(d_corr, al, bh, kIdesc, j ? 1u : fresh_corr);  // whole K
             mma_tf32(d_corr, ah, bl, kIdesc, 1);
-            if (COSSIN_TC_PASSES == 4) mma_tf32(d_corr, al, bl, kIdesc, 1);
+            mma_tf32(d_corr, al, bl, kIdesc, 1);
           }
           mma_commit(&empty_bar[st]);
           kb_consumed = kb + 1;
