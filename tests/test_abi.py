@@ -163,3 +163,33 @@ def test_cs_select_errors(L):
         with pytest.raises(_lib.CossinError) as e:
             api.cs_select(bad, 0)
         assert e.value.status == st
+
+
+def test_matmul_argument_errors_before_any_gpu_work(L):
+    nul = ctypes.c_void_p(0)
+    p = ctypes.c_void_p(4096)
+    assert L.cossin_matmul(nul, nul, 0, 0, nul, nul) == _lib.CS_OK  # n = 0: no-op
+    assert L.cossin_matmul(nul, nul, -1, 0, nul, nul) == _lib.CS_EINVAL
+    assert L.cossin_matmul(p, p, 8, 9, p, nul) == _lib.CS_EINVAL  # unknown precision
+    assert L.cossin_matmul(nul, p, 8, 0, ctypes.c_void_p(1 << 20), nul) == _lib.CS_EINVAL  # null X
+    assert L.cossin_matmul(p, p, 8, 0, p, nul) == _lib.CS_EINVAL  # P overlaps X
+    assert b"overlap" in L.cossin_last_error()
+    for prec in (_lib.CS_FP64_EMU, _lib.CS_SPLIT_BF16):
+        assert L.cossin_matmul(p, p, 8193, prec, ctypes.c_void_p(1 << 40), nul) == _lib.CS_EINVAL
+        assert b"8192" in L.cossin_last_error()
+
+
+def test_batched_argument_errors_before_any_gpu_work(L):
+    size = ctypes.c_size_t()
+    ns = (ctypes.c_int64 * 3)(8, 300, 16)
+    assert L.cossin_batched_workspace_size(3, ns, ctypes.byref(size)) == _lib.CS_EINVAL
+    assert b"256" in L.cossin_last_error()
+    ns_ok = (ctypes.c_int64 * 3)(8, 256, 0)
+    assert L.cossin_batched_workspace_size(3, ns_ok, ctypes.byref(size)) == _lib.CS_OK and size.value > 0
+    big = size.value  # sized by the largest order (per-CTA slices), not by the count
+    ns_small = (ctypes.c_int64 * 3)(8, 16, 0)
+    assert L.cossin_batched_workspace_size(3, ns_small, ctypes.byref(size)) == _lib.CS_OK and 0 < size.value < big
+    assert L.cossin_batched_workspace_size(-1, ns_ok, ctypes.byref(size)) == _lib.CS_EINVAL
+    assert L.cossin_batched_workspace_size((1 << 30) + 1, ns_ok, ctypes.byref(size)) == _lib.CS_EINVAL
+    assert L.cossin_batched_workspace_size(2, None, ctypes.byref(size)) == _lib.CS_EINVAL
+    assert L.cossin_batched_workspace_size(2, ns_ok, None) == _lib.CS_EINVAL
