@@ -193,3 +193,18 @@ def test_batched_argument_errors_before_any_gpu_work(L):
     assert L.cossin_batched_workspace_size((1 << 30) + 1, ns_ok, ctypes.byref(size)) == _lib.CS_EINVAL
     assert L.cossin_batched_workspace_size(2, None, ctypes.byref(size)) == _lib.CS_EINVAL
     assert L.cossin_batched_workspace_size(2, ns_ok, None) == _lib.CS_EINVAL
+
+
+@pytest.mark.parametrize("prec,table", [(_lib.CS_FP64, 0), (_lib.CS_FP64_EMU, 0), (_lib.CS_FP32, 1),
+                                        (_lib.CS_SPLIT_TF32, 1), (_lib.CS_SPLIT_EMU, 1), (_lib.CS_SPLIT_BF16, 1)])
+def test_precision_selects_its_table(L, prec, table):
+    """FP64-accurate kinds use Table 1 (u = 2^-53), the FP32-accurate and
+    split kinds Table 2 (u = 2^-24); an n = 0 call reports it without device
+    work, for cossin_ex and for cossin_cs."""
+    nul = ctypes.c_void_p(0)
+    info = _lib.CsInfo()
+    assert L.cossin_ex(nul, 0, prec, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_OK
+    assert info.table == table
+    info = _lib.CsInfo()
+    assert L.cossin_cs(nul, 0, 1.0, prec, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_OK
+    assert info.table == table
