@@ -122,32 +122,28 @@ Layout make_layout(int64_t n, int prec, bool with_outputs) {
   };
   L.norm_partial = take(sizeof(double) * (size_t)norm1_scratch_elems(n));
   L.norm_out = take(sizeof(double));
-  if (f64_storage((cs_prec)prec)) {
-    for (int w = 0; w < kWorkSlots; ++w) L.w[w] = take(sizeof(double) * n2);
-    L.ping64[0] = take(sizeof(double) * 2 * n2);
-    L.ping64[1] = take(sizeof(double) * 2 * n2);
-    if (prec != CS_FP64) {
-      // the stacked eight-slice double-angle product is the largest (the
-      // four-slice chain products of CS_SPLIT_BF16 need less)
-      L.ozaki_bytes = ozaki_dims(2 * n, n, n).total;
-      L.ozaki = take(L.ozaki_bytes);
-    }
-  } else {
+  // Every precision keeps its intermediates in FP64: the double-angle
+  // recurrence amplifies the rounding of stored intermediates far beyond
+  // FP32 level at ||A||_1 near 64 (an FP32-stored evaluation with exactly
+  // rounded products is 1.3e-5 from the FP64 result on a 1 x 1 matrix).
+  for (int w = 0; w < kWorkSlots; ++w) L.w[w] = take(sizeof(double) * n2);
+  L.ping64[0] = take(sizeof(double) * 2 * n2);
+  L.ping64[1] = take(sizeof(double) * 2 * n2);
+  if (prec == CS_FP32) L.a64 = take(sizeof(double) * n2);  // the FP32 input in FP64
+  if (prec == CS_SPLIT_TF32 || prec == CS_SPLIT_EMU) {
+    // operand splits of the four-pass TF32 chain products and their raw product
     L.ld32 = (n + 31) / 32 * 32;
     const size_t sz = sizeof(float) * (size_t)n * (size_t)L.ld32;
     for (int k = 0; k < 4; ++k) L.a4[k] = take(sz);
     for (int w = 0; w < kWorkSlots; ++w)
       for (int k = 0; k < 4; ++k) L.w4[w][k] = take(sz);
-    for (int p = 0; p < 2; ++p)
-      for (int k = 0; k < 4; ++k) L.ping4[p][k] = take(k < 2 ? 2 * sz : sz);
-    if (prec == CS_SPLIT_TF32 || prec == CS_SPLIT_EMU) {
-      L.ping64[0] = take(sizeof(double) * 2 * n2);
-      L.ping64[1] = take(sizeof(double) * 2 * n2);
-    }
-    if (prec == CS_SPLIT_EMU) {
-      L.ozaki_bytes = ozaki_dims(2 * n, n, n).total;
-      L.ozaki = take(L.ozaki_bytes);
-    }
+    for (int k = 0; k < 4; ++k) L.c4[k] = take(sz);
+    L.p32 = take(sz);
+  }
+  if (uses_emu((cs_prec)prec)) {
+    // the stacked double-angle product is the largest emulated one
+    L.ozaki_bytes = ozaki_dims(2 * n, n, n, 1, square_slices((cs_prec)prec)).total;
+    L.ozaki = take(L.ozaki_bytes);
   }
   if (with_outputs) {
     const size_t el = prec == CS_FP32 ? sizeof(float) : sizeof(double);
@@ -361,6 +357,29 @@ cs_status run_f64(const double* A, int64_t n, double* C, double* S, char* ws, co
 
 }  // namespace
 
+// The FP64 executor for every precision whose products take FP64 operands
+// (all but the TF32 split forms).  CS_FP32 converts its input to FP64 once,
+// runs the plan with four-slice products and FP64 intermediates, and rounds
+// C and S to FP32 once at the end (the FP64 result of the last step lands in
+// ping[s & 1], which the last double-angle step does not read).
+cs_status run_plan_f64(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* w, const Layout& L,
+                       const PlanSpec& spec, cudaStream_t stream) {
+  if (prec != CS_FP32)
+    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, chain_product(prec, w, L),
+                   f64_product(prec, w, L), stream);
+  const int64_t n2 = n * n;
+  double* a64 = (double*)(w + L.a64);
+  CS_CHECK(convert_f32_f64((const float*)A, a64, n2, stream));
+  double* fin = (double*)(w + L.ping64[spec.s & 1]);
+  CS_CHECK(run_f64(a64, n, fin, fin + n2, w, L, spec, chain_product(prec, w, L), f64_product(prec, w, L), stream));
+  CS_CHECK(convert_f64_f32(fin, (float*)C, n2, stream));
+  return convert_f64_f32(fin + n2, (float*)S, n2, stream);
+}
+
+namespace {
+
+}  // namespace
+
 // Double-angle steps (Sec. 1): [C'; S'] = [C; S] C with C' = 2X - I, S' = 2X,
 // one stacked 2n x n x n product per step, ping-ponging between the buffers.
 cs_status F64Product::operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
@@ -369,19 +388,22 @@ cs_status F64Product::operator()(const double* X, const double* Y, int64_t M, in
   return gemm_f64(X, Y, M, N, K, K, N, false, false, e, N, 1, 0, 0, 0, stream);
 }
 
+int square_slices(cs_prec prec) { return prec == CS_FP32 ? kOzakiSlicesSplit : kOzakiSlices; }
+
 F64Product f64_product(cs_prec prec, char* ws, const Layout& L) {
   F64Product p;
   if (uses_emu(prec)) {
     p.emu_work = ws + L.ozaki;
     p.emu_bytes = L.ozaki_bytes;
     p.err = tc_error_word();
+    p.slices = square_slices(prec);
   }
   return p;
 }
 
 F64Product chain_product(cs_prec prec, char* ws, const Layout& L) {
   F64Product p = f64_product(prec, ws, L);
-  if (prec == CS_SPLIT_BF16) p.slices = kOzakiSlicesSplit;
+  if (prec == CS_SPLIT_BF16 || prec == CS_FP32) p.slices = kOzakiSlicesSplit;
   return p;
 }
 
@@ -407,9 +429,11 @@ cs_status square_f64(double* const ping[2], int64_t n, int s, double* C, double*
   return CS_OK;
 }
 
-bool uses_emu(cs_prec p) { return p == CS_FP64_EMU || p == CS_SPLIT_EMU || p == CS_SPLIT_BF16; }
+bool uses_emu(cs_prec p) {
+  return p == CS_FP64_EMU || p == CS_SPLIT_EMU || p == CS_SPLIT_BF16 || p == CS_FP32;
+}
 
-bool f64_storage(cs_prec p) { return p == CS_FP64 || p == CS_FP64_EMU || p == CS_SPLIT_BF16; }
+bool f64_operands(cs_prec p) { return p != CS_SPLIT_TF32 && p != CS_SPLIT_EMU; }
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
@@ -457,7 +481,7 @@ namespace {
 
 }  // namespace
 
-cs_status run_tf32(const void* A, int64_t n, cs_prec prec, void* C, void* S, char* ws, const Layout& L,
+cs_status run_tf32(const double* A, int64_t n, cs_prec prec, double* C, double* S, char* ws, const Layout& L,
                    const PlanSpec& P, cudaStream_t stream);
 cs_status matmul_tf32(const void* X, const void* Y, int64_t n, bool f64_io, void* P, cudaStream_t stream);
 
@@ -505,10 +529,8 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   const int prods = products_of(m) + 2 * s;
   if (info) *info = cs_info{nrm, m, s, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
   const PlanSpec spec = cossin_spec(m, s, scale);
-  if (f64_storage(prec))
-    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, chain_product(prec, w, L),
-                   f64_product(prec, w, L), stream);
-  return run_tf32(A, n, prec, C, S, w, L, spec, stream);
+  if (f64_operands(prec)) return run_plan_f64(A, n, prec, C, S, w, L, spec, stream);
+  return run_tf32((const double*)A, n, prec, (double*)C, (double*)S, w, L, spec, stream);
 }
 
 cs_status cs_check_args(int64_t n, double t, cs_prec prec, int32_t force_f, int32_t force_s) {
@@ -560,10 +582,8 @@ cs_status cs_impl(const void* A, int64_t n, double t, cs_prec prec, void* C, voi
   const int prods = cs_family_products(f) + 2 * sg;
   if (info) *info = cs_info{normB, f, sg, prods, table, 2.0 * (double)n * (double)n * (double)n * prods};
   const PlanSpec spec = cs_spec(f, sg, t);
-  if (f64_storage(prec))
-    return run_f64((const double*)A, n, (double*)C, (double*)S, w, L, spec, chain_product(prec, w, L),
-                   f64_product(prec, w, L), stream);
-  return run_tf32(A, n, prec, C, S, w, L, spec, stream);
+  if (f64_operands(prec)) return run_plan_f64(A, n, prec, C, S, w, L, spec, stream);
+  return run_tf32((const double*)A, n, prec, (double*)C, (double*)S, w, L, spec, stream);
 }
 
 }  // namespace cs
@@ -645,24 +665,43 @@ cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, v
   if (cs::overlaps(P, bytes, X, bytes) || cs::overlaps(P, bytes, Y, bytes))
     return cs::fail(CS_EINVAL, "P must not overlap X or Y");
   cudaStream_t st = (cudaStream_t)stream;
-  if (cs::f64_storage(prec)) {
-    cs::Epilogue<double> e;
-    e.n_out = 1;
+  if (!cs::f64_operands(prec)) return cs::matmul_tf32(X, Y, n, true, P, st);
+  cs::Epilogue<double> e;
+  e.n_out = 1;
+  e.alpha[0] = 1.0;
+  if (prec == CS_FP64) {
     e.out[0] = (double*)P;
-    e.alpha[0] = 1.0;
-    if (prec == CS_FP64)
-      return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
-    cs::F64Product prod;
-    prod.slices = prec == CS_SPLIT_BF16 ? cs::kOzakiSlicesSplit : cs::kOzakiSlices;
-    prod.emu_bytes = cs::ozaki_dims(n, n, n, 1, prod.slices).total;
-    prod.err = cs::tc_error_word();
-    if (!prod.err) return cs::fail(CS_ECUDA, "cannot resolve the device error word");
-    CS_CUDA_CHECK(cudaMallocAsync(&prod.emu_work, prod.emu_bytes, st));
-    cs_status rc = prod((const double*)X, (const double*)Y, n, n, n, e, st);
-    cudaFreeAsync(prod.emu_work, st);
-    return rc;
+    return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
   }
-  return cs::matmul_tf32(X, Y, n, prec != CS_FP32, P, st);
+  // Emulated products; CS_FP32 takes FP32 operands to FP64 and rounds the
+  // product to FP32 once.
+  const bool f32 = prec == CS_FP32;
+  const size_t n2 = (size_t)n * (size_t)n;
+  cs::F64Product prod;
+  prod.slices = (prec == CS_SPLIT_BF16 || f32) ? cs::kOzakiSlicesSplit : cs::kOzakiSlices;
+  prod.emu_bytes = cs::ozaki_dims(n, n, n, 1, prod.slices).total;
+  prod.err = cs::tc_error_word();
+  if (!prod.err) return cs::fail(CS_ECUDA, "cannot resolve the device error word");
+  const size_t conv = f32 ? (3 * sizeof(double) * n2 + 255) & ~(size_t)255 : 0;
+  char* buf = nullptr;
+  CS_CUDA_CHECK(cudaMallocAsync((void**)&buf, conv + prod.emu_bytes, st));
+  prod.emu_work = buf + conv;
+  const double* X64 = (const double*)X;
+  const double* Y64 = (const double*)Y;
+  e.out[0] = (double*)P;
+  cs_status rc = CS_OK;
+  if (f32) {
+    double* x = (double*)buf;
+    X64 = x;
+    Y64 = x + n2;
+    e.out[0] = x + 2 * n2;
+    rc = cs::convert_f32_f64((const float*)X, x, (int64_t)n2, st);
+    if (rc == CS_OK) rc = cs::convert_f32_f64((const float*)Y, x + n2, (int64_t)n2, st);
+  }
+  if (rc == CS_OK) rc = prod(X64, Y64, n, n, n, e, st);
+  if (rc == CS_OK && f32) rc = cs::convert_f64_f32(e.out[0], (float*)P, (int64_t)n2, st);
+  cudaFreeAsync(buf, st);
+  return rc;
 }
 
 cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,

@@ -127,6 +127,9 @@ cs_status norm1_batched_f64(const double* A, int64_t n, int64_t count, double* o
 
 // dst[i] = scale * src[i], i < count (FP64).
 cs_status scale_f64(const double* src, double* dst, int64_t count, double scale, cudaStream_t stream);
+// Element-wise FP32 -> FP64 (exact) and FP64 -> FP32 (rounded to nearest).
+cs_status convert_f32_f64(const float* src, double* dst, int64_t count, cudaStream_t stream);
+cs_status convert_f64_f32(const double* src, float* dst, int64_t count, cudaStream_t stream);
 
 // The executors behind the ABI (cossin_api.cu, adjoint.cu): cos/sin and the
 // adjoint of scale * A.
@@ -136,8 +139,15 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
                         cs_info* infos_host, cudaStream_t stream, bool emu = false);
 cs_status check_prec(cs_prec prec);
-bool uses_emu(cs_prec p);      // CS_FP64_EMU, CS_SPLIT_EMU, CS_SPLIT_BF16: sliced BF16 tensor-core products
-bool f64_storage(cs_prec p);  // CS_FP64, CS_FP64_EMU, CS_SPLIT_BF16: the FP64 executor (FP64 intermediates)
+// Every precision keeps FP64 intermediates.  uses_emu: some products are
+// sliced BF16 tensor-core products (CS_FP64_EMU, CS_SPLIT_EMU, CS_SPLIT_BF16,
+// CS_FP32); f64_operands: every product takes FP64 operands (all but the TF32
+// split forms, whose chain products take (hi, lo) TF32 splits).
+bool uses_emu(cs_prec p);
+bool f64_operands(cs_prec p);
+// Slices of the emulated double-angle products of a precision (four for
+// CS_FP32, eight for the FP64-class ones).
+int square_slices(cs_prec p);
 size_t elem_size(cs_prec p);
 bool overlaps(const void* a, size_t na, const void* b, size_t nb);
 

@@ -53,21 +53,23 @@ PlanSpec cossin_spec(int m, int s, double scale = 1.0);
 PlanSpec cs_spec(int family, int sigma, double t);
 int cs_products(int family);
 
-// Byte offsets into the caller's workspace.
-//  FP64:       w[8] (n x n doubles), ping64[2] (stacked [C; S], 2n x n doubles)
-//  TF32 modes: every slot is four n x ld32 float arrays {hi, lo, hi^T, lo^T}
-//              (a4 for A, w4 for W0..W7); ping4[p] = {[C;S] hi, [C;S] lo,
-//              C^T hi, C^T lo} with the first two 2n x ld32; split mode adds
-//              ping64 for the FP64 double-angle steps.
+// Byte offsets into the caller's workspace.  Every precision: w[8] (n x n
+// doubles), ping64[2] (stacked [C; S], 2n x n doubles).  CS_FP32 adds a64
+// (its input in FP64).  The TF32 split forms add the (hi, lo) TF32 operand
+// splits {hi, lo, hi^T, lo^T} (n x ld32 floats each) of A (a4), W0..W7 (w4)
+// and C (c4), and p32, the raw product of one chain step.  The emulated
+// precisions add the scratch of one emulated product.
 struct Layout {
   size_t norm_partial = 0, norm_out = 0;
   size_t w[kWorkSlots] = {};
   size_t ping64[2] = {};
+  size_t a64 = 0;
   int64_t ld32 = 0;
   size_t a4[4] = {};
   size_t w4[kWorkSlots][4] = {};
-  size_t ping4[2][4] = {};
-  size_t ozaki = 0, ozaki_bytes = 0;  // scratch of one emulated product (CS_FP64_EMU, *_EMU, *_BF16)
+  size_t c4[4] = {};
+  size_t p32 = 0;
+  size_t ozaki = 0, ozaki_bytes = 0;  // scratch of one emulated product
   size_t out_c = 0, out_s = 0;  // n x n C and S of the precision's type (with_outputs)
   size_t total = 0;
 };
@@ -85,8 +87,8 @@ struct F64Product {
   cs_status operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
                        const Epilogue<double>& e, cudaStream_t stream) const;
 };
-// The product of the double-angle steps for `prec` (the Taylor chain's, too,
-// but for CS_SPLIT_BF16, whose chain takes chain_product).
+// The product of the double-angle steps for `prec`, and that of the Taylor
+// chain (four slices for CS_SPLIT_BF16 and CS_FP32).
 F64Product f64_product(cs_prec prec, char* ws, const Layout& L);
 F64Product chain_product(cs_prec prec, char* ws, const Layout& L);
 

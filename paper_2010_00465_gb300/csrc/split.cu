@@ -16,14 +16,17 @@ __device__ int g_tc_error;
 template <typename T>
 __global__ void __launch_bounds__(256) split_kernel(const T* __restrict__ src, int64_t n, int64_t ld,
                                                     float* __restrict__ hi, float* __restrict__ lo,
-                                                    float* __restrict__ hiT, float* __restrict__ loT, double scale) {
+                                                    float* __restrict__ hiT, float* __restrict__ loT, double scale,
+                                                    bool zero_diag) {
   __shared__ float tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int64_t r = r0 + i, c = c0 + threadIdx.x;
     float v = 0.f;
-    if (r < n && c < n) {
+    if (r < n && c < n && !(zero_diag && r == c)) {
       v = scale == 1.0 ? (float)src[r * n + c] : (float)((double)src[r * n + c] * scale);
+    }
+    if (r < n && c < n) {
       const float h = ptx::tf32_rna(v);
       hi[r * ld + c] = h;
       lo[r * ld + c] = COSSIN_LO(v - h);
@@ -55,11 +58,11 @@ __global__ void __launch_bounds__(256) combine_kernel(const float* __restrict__ 
 
 template <typename T>
 cs_status split_impl(const T* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                     double scale, cudaStream_t stream) {
+                     double scale, bool zero_diag, cudaStream_t stream) {
   if (n <= 0) return CS_OK;
   ProfScope prof(CS_KERNEL_OTHER, (double)n * n * (sizeof(T) + (hiT ? 16.0 : 8.0)), stream);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
-  split_kernel<T><<<grid, block, 0, stream>>>(src, n, ld, hi, lo, hiT, loT, scale);
+  split_kernel<T><<<grid, block, 0, stream>>>(src, n, ld, hi, lo, hiT, loT, scale, zero_diag);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
@@ -78,12 +81,12 @@ cs_status combine_impl(const float* hi, const float* lo, int64_t n, int64_t ld, 
 }  // namespace
 
 cs_status split_f32(const float* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                    cudaStream_t stream, double scale) {
-  return split_impl<float>(src, n, ld, hi, lo, hiT, loT, scale, stream);
+                    cudaStream_t stream, double scale, bool zero_diag) {
+  return split_impl<float>(src, n, ld, hi, lo, hiT, loT, scale, zero_diag, stream);
 }
 cs_status split_f64(const double* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                    cudaStream_t stream, double scale) {
-  return split_impl<double>(src, n, ld, hi, lo, hiT, loT, scale, stream);
+                    cudaStream_t stream, double scale, bool zero_diag) {
+  return split_impl<double>(src, n, ld, hi, lo, hiT, loT, scale, zero_diag, stream);
 }
 
 namespace {
@@ -92,7 +95,30 @@ __global__ void __launch_bounds__(256) scale_kernel(const double* __restrict__ s
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = scale * src[i];
 }
+
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) convert_kernel(const S* __restrict__ src, D* __restrict__ dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (D)src[i];
+}
+
+template <typename S, typename D>
+cs_status convert(const S* src, D* dst, int64_t count, cudaStream_t stream) {
+  if (count <= 0) return CS_OK;
+  ProfScope prof(CS_KERNEL_OTHER, (double)(sizeof(S) + sizeof(D)) * (double)count, stream);
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
+  convert_kernel<S, D><<<blocks, 256, 0, stream>>>(src, dst, count);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
 }  // namespace
+
+cs_status convert_f32_f64(const float* src, double* dst, int64_t count, cudaStream_t stream) {
+  return convert<float, double>(src, dst, count, stream);
+}
+cs_status convert_f64_f32(const double* src, float* dst, int64_t count, cudaStream_t stream) {
+  return convert<double, float>(src, dst, count, stream);
+}
 
 cs_status scale_f64(const double* src, double* dst, int64_t count, double scale, cudaStream_t stream) {
   if (count <= 0) return CS_OK;

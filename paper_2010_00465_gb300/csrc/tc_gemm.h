@@ -46,11 +46,13 @@ cs_status gemm_tf32(const TcOperand& X, const TcOperand& YT, int64_t M, int64_t 
 
 // (hi, lo) split of scale * (an n x n row-major matrix, FP32 or FP64 source,
 // leading dimension n) into padded (ld) hi/lo and, if hiT is non-null, the
-// transposed split.  The scaled value is rounded to FP32 once.
+// transposed split.  The scaled value is rounded to FP32 once.  With
+// zero_diag the diagonal of the splits is 0 (the chain products add the
+// diagonal terms exactly in FP64).
 cs_status split_f32(const float* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                    cudaStream_t stream, double scale = 1.0);
+                    cudaStream_t stream, double scale = 1.0, bool zero_diag = false);
 cs_status split_f64(const double* src, int64_t n, int64_t ld, float* hi, float* lo, float* hiT, float* loT,
-                    cudaStream_t stream, double scale = 1.0);
+                    cudaStream_t stream, double scale = 1.0, bool zero_diag = false);
 
 // dst (n x n, leading dimension n) = hi + lo (padded ld), as FP32 or FP64.
 cs_status combine_f32(const float* hi, const float* lo, int64_t n, int64_t ld, float* dst, cudaStream_t stream);

@@ -11,13 +11,7 @@ from paper_2010_00465_gb300 import _lib, api, inputs
 pytestmark = pytest.mark.gpu
 
 
-def tol32(n, nrm):
-    """Same bounds as the single-matrix FP32 path (see test_gpu_tf32.tol32)."""
-    if n < 32:
-        return 2e-5 * max(1.0, nrm / 8.0)
-    if nrm > 8.0 and n < 1024:
-        return 1e-4
-    return 2e-5
+TOL32 = 2e-5
 
 
 def relfro(X, Y):
@@ -33,7 +27,7 @@ def check_against_oracle(A32, C, S, info):
     assert info["norm1"] == pytest.approx(nrm, rel=1e-13, abs=0.0)
     assert (int(info["m"]), int(info["s"])) == oracle.select(nrm, "single")
     Co, So, _ = oracle.cossin(A, "single", m=int(info["m"]), s=int(info["s"]))
-    t = tol32(A.shape[0], nrm)
+    t = TOL32
     ec, es = relfro(C, Co), relfro(S, So)
     assert ec <= t and es <= t, (A.shape[0], nrm, ec, es)
 

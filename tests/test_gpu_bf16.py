@@ -106,8 +106,7 @@ def test_cs_and_unitary_forms(n, nrm):
     Co, So, io = oracle.cs(A, t, prec="single")
     C, S, info = api.cossin_cs(dev(A), t, "split_bf16", return_info=True)
     assert (info["m"], info["s"], info["table"]) == (io["m"], io["s"], 1)
-    tol = TOL32 * max(1.0, t * t * nrm / 8.0)
-    assert relfro(C.cpu(), Co) <= tol and relfro(S.cpu(), So) <= tol
+    assert relfro(C.cpu(), Co) <= TOL32 and relfro(S.cpu(), So) <= TOL32
     Uo, _ = oracle.unitary(A, 0.8, prec="single")
     Ug = api.unitary(dev(A), 0.8, "split_bf16")
-    assert relfro(Ug.cpu().numpy(), Uo) <= TOL32 * max(1.0, 0.8 * nrm / 8.0)
+    assert relfro(Ug.cpu().numpy(), Uo) <= TOL32
