@@ -1,18 +1,50 @@
 // batched.cu -- cos/sin of many FP32 matrices of uneven order and norm, each
-// with its own (2m, s), in one persistent launch.
+// with its own (2m, s), in one persistent launch with the products on the
+// tensor cores.
 //
-// Every CTA takes matrices from a device work queue (longest first: the host
-// orders the batch by n^3), computes ||A||_1 (FP64 accumulation), chooses
-// (2m, s) from Table 2 on the device, and runs the same product plan as the
-// single-matrix path: Pi_2m products with the scheme's linear combinations
-// fused into each product's epilogue, then s double-angle products
-// [C; S] C.  Orders are at most kMaxOrder = 256, so the products are CTA-level
-// FP32 FMA tiles (IEEE accumulation; intermediates stay in the CTA's own
-// workspace slice, hot in L2).  Tile shapes (64 or 128 rows/columns per CTA
-// tile for orders above 64) and occupancies are timed by the plan's autotuner.
+// Every CTA (one per SM) takes matrices from a device work queue (largest
+// order first: the host orders the batch by n), computes ||A||_1 (FP64 sums,
+// warp-shuffle maximum), chooses (2m, s) from Table 2 on the device and runs
+// the same product plan as the single-matrix path: the Pi_2m products of the
+// factorised scheme with its linear combinations fused into each product's
+// epilogue, then s double-angle products [C; S] C.
+//
+// Precision.  The double-angle recurrence C <- 2C^2 - I amplifies the
+// rounding of the chain's stored results by two orders of magnitude at
+// ||A||_1 near 64 (FP32 storage with exactly rounded products ends 1.3e-5
+// from the FP64 result on a 1 x 1 matrix, 8e-6 at n = 128).  So the chain
+// keeps its intermediates as double-float pairs (hi, lo) of FP32 values
+// (about 48 bits) with double-float epilogue arithmetic on the FP32 pipes
+// (GB300's FP64 rate is 1/64 of FP32's), and the double-angle steps, whose
+// own rounding is amplified far less, store FP32.
+//
+// Products on the tensor cores.  Each operand is cut into four 7-bit
+// fixed-point slices, rows of X scaled by 2^-e_r and columns of Y by 2^-f_c
+// (powers of two from a pre-pass over the operands):
+//   X[r][k] 2^(7-e_r) = a_0 + a_1 2^-7 + a_2 2^-14 + a_3 2^-21 (+ < 2^-22),
+// with integer digits |a_0| <= 128, |a_p| <= 64, exact in BF16.  The ten
+// slice products with p + q <= 3 run as kind::f16 tcgen05 MMAs (M = 128,
+// N <= 128, K = 16) into one FP32 TMEM accumulator per level L = p + q; every
+// term is an integer and for K <= 256 every level stays below 2^24, so each
+// level sum is exact.  The epilogue combines the levels (double-float for the
+// chain, FP32 for the squaring) and applies 2^(e_r + f_c - 14).  The dropped
+// digits leave at most 2^-28 K max|X[r][.]| max|Y[.][c]| per entry.  The
+// chain's matrices are often dominated by their diagonal (C_j = a_0 I + ...),
+// which would set the fixed-point grid of the whole row, so X[r][r mod K] is
+// left out of the slices of X and X[r][d] Y[d][c] (d = r mod K) is added in
+// the epilogue; one operand suffices, since the error is then relative to
+// the off-diagonal maxima of X's rows.
+//
+// Data movement.  The operands live in the CTA's workspace slice (L2-hot for
+// the common orders); the slicing warps read them with coalesced loads and
+// write the slices into 64-byte-swizzled K-major shared memory (two stages
+// of 32 k, each written while the tensor core reads the other), one thread
+// issues the MMAs, and the eight warps drain TMEM through per-warp
+// shared-memory tiles so that the epilogue's loads and stores walk rows.
 //
 // Graph capture: the plan records the queue reset and the persistent launch
 // in a CUDA graph once; each replay is one graph launch.
+#include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -25,29 +57,60 @@
 
 #include "internal.cuh"
 #include "plan.h"
+#include "sm100_ptx.cuh"
+#include "tc_gemm.h"
 #include "theta_table.cuh"
 
 namespace cs {
 namespace bt {
 
-constexpr int kThreads = 256;
-constexpr int kMaxOrder = 256;
-constexpr int kBK = 16;
-constexpr int kSlots = 8 + 4;  // W0..W7 and two stacked [C; S] buffers (2 each)
+using namespace ptx;
 
-// One product of a plan in dense form: distinct input slots in[], and for
-// every output t: out_t = alpha_t P + gamma_t I + sum_q beta[t][q] in_q
-// + sum_{u<t} delta[t][u] out_u; scale[t] multiplies alpha_t by 4^-s (1) or
-// 2^-s (2).
+constexpr int kMaxWarps = 16;
+constexpr int kMaxOrder = 256;
+constexpr int kMaxM = 2 * kMaxOrder;  // rows of the stacked double-angle operand
+constexpr int kBM = 128;              // tile rows = TMEM lanes
+constexpr int kKc = 32;               // k per stage (rows of 64 bytes of BF16)
+constexpr int kSlices = 4;
+constexpr int kDfSlots = 10;          // W0..W7, C, S as double-float pairs
+constexpr int kFloatsPerN2 = 2 * kDfSlots + 4;  // + two stacked FP32 [C; S] buffers
+
+// Tiles of 128 x NT: four level accumulators of NT columns fill 4 NT TMEM
+// columns, so NT = 128 runs one CTA per SM and NT = 64 two.  The epilogue
+// stages a tile's product (two planes of 128 x NT floats) in the stages,
+// which are idle once the tile's MMAs are done.
+template <int NT>
+struct Cfg {
+  static constexpr int kThreads = NT == 128 ? 512 : 256;  // 512 threads per SM either way
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kABytes = kBM * kKc * 2;  // one A slice of a stage
+  static constexpr int kBBytes = NT * kKc * 2;   // one B slice of a stage
+  static constexpr int kStageBytes = kSlices * (kABytes + kBBytes);
+  static constexpr int kStages = 2;
+  static constexpr int kSmem = kStages * kStageBytes + 1024;
+  static constexpr uint32_t kTmemCols = kSlices * NT;
+  static constexpr int kCtasPerSm = 512 / (kSlices * NT);
+  static_assert(2 * kBM * NT * 4 <= kStages * kStageBytes, "the staged tile fits the stages");
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+  static_assert(kTmemCols <= 512, "TMEM columns");
+};
+
+// One product of a plan in dense form (see upload_plans): distinct input
+// slots in[], and for every output t: out_t = alpha_t P + gamma_t I
+// + sum_q beta[t][q] in_q + delta[t] out_0, each coefficient a double-float
+// pair; scale[t] multiplies alpha_t by 4^-s (1) or 2^-s (2).  (The schemes
+// of Sec. 2.1 read at most four earlier matrices per product and chain
+// outputs only to the first output of the same product.)
+constexpr int kMaxIn = 4;
 struct DStep {
   int X, Y, nout, nin;
   int out[EPI_MAX_OUT];
-  int in[EPI_MAX_IN];
+  int in[kMaxIn];
   int scale[EPI_MAX_OUT];
-  float alpha[EPI_MAX_OUT];
-  float gamma[EPI_MAX_OUT];
-  float beta[EPI_MAX_OUT][EPI_MAX_IN];
-  float delta[EPI_MAX_OUT][EPI_MAX_OUT];
+  float2 alpha[EPI_MAX_OUT];
+  float2 gamma[EPI_MAX_OUT];
+  float2 beta[EPI_MAX_OUT][kMaxIn];
+  float2 delta[EPI_MAX_OUT];
 };
 struct DPlan {
   int nsteps;
@@ -63,190 +126,549 @@ struct Desc {
   int64_t n;
 };
 
-struct Slots {
-  float* p[SL_COUNT];
+// ------------------------------------------------------------ double-float --
+// Pairs (hi, lo) with |lo| <= ulp(hi) / 2: Knuth's TwoSum, the fast two-sum
+// (|a| >= |b|) and an FMA-based product, as in Dekker's double-length
+// arithmetic.
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ dfl df_mul(float2 c, dfl x) {
+  const float p = c.x * x.hi;
+  float e = fmaf(c.x, x.hi, -p);
+  e = fmaf(c.x, x.lo, e);
+  e = fmaf(c.y, x.hi, e);
+  return fast_two_sum(p, e);
+}
+// Accumulation without renormalising after every term: acc.hi carries the
+// leading sum, acc.lo the exact errors of the leading additions plus the low
+// parts (renormalised once at the end with fast_two_sum).
+__device__ __forceinline__ dfl df_mul_raw(float2 c, dfl x) {
+  const float p = c.x * x.hi;
+  float e = fmaf(c.x, x.hi, -p);
+  e = fmaf(c.x, x.lo, e);
+  return {p, fmaf(c.y, x.hi, e)};
+}
+__device__ __forceinline__ void df_acc(dfl& acc, dfl t) {
+  const dfl s = two_sum(acc.hi, t.hi);
+  acc.hi = s.hi;
+  acc.lo += s.lo + t.lo;
+}
+
+// ------------------------------------------------------------------ operands --
+// An operand matrix: rows [0, split) from (hi, lo), rows [split, ...) from
+// (hi2, lo2) (the stacked [C; S]); lo null for FP32 values.  Leading dimension n.
+struct Opnd {
+  const float* hi;
+  const float* lo;
+  const float* hi2;
+  const float* lo2;
+  int split;
+};
+__device__ __forceinline__ dfl opnd_get(const Opnd& o, int r, int k, int n) {
+  const float* h = o.hi;
+  const float* l = o.lo;
+  if (r >= o.split) {
+    h = o.hi2;
+    l = o.lo2;
+    r -= o.split;
+  }
+  const int idx = r * n + k;  // n <= 256
+  return {h[idx], l ? l[idx] : 0.f};
+}
+
+// Scale factors of a row / column whose largest |hi| has the bit pattern
+// `bits`: |x| < 2^e, slicing scale 2^(7-e), product scale 2^(e-7).  e is kept
+// >= -100 (a larger e is still valid, with fewer digits), so both are normal.
+__device__ __forceinline__ void scales_of(unsigned bits, float* slice_sc, float* prod_sc) {
+  const float m = __uint_as_float(bits);
+  int e = 0;
+  if (m > 0.f && isfinite(m)) frexpf(m, &e);
+  e = max(e, -100);
+  *slice_sc = ldexpf(1.f, 7 - e);
+  *prod_sc = ldexpf(1.f, e - 7);
+}
+
+// The four digits of x = hi + lo in units of the slicing scale sc.
+__device__ __forceinline__ void digits(dfl x, float sc, float d[kSlices]) {
+  const float s = x.hi * sc;  // |s| < 128, exact
+  d[0] = rintf(s);
+  float r = (s - d[0]) + x.lo * sc;  // s - d[0] is exact, |r| <= 1/2 (+ lo)
+  r *= 128.f;
+  d[1] = rintf(r);
+  r = (r - d[1]) * 128.f;
+  d[2] = rintf(r);
+  r = (r - d[2]) * 128.f;
+  d[3] = rintf(r);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);  // integers |x| <= 128: exact
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Byte offset of the 4-byte word holding k, k + 1 (k even, k < 32) of row r in
+// a K-major tile with 64-byte rows and the 64-byte swizzle (16-byte chunk c of
+// row r stored at c ^ ((r >> 1) & 3); 512-byte atoms of 8 rows).
+__device__ __forceinline__ uint32_t swz64(int r, int k) {
+  return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + ((k & 7) >> 1) * 4);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------------------------ shared --
+struct Shared {
+  float sx[kMaxM], px[kMaxM];          // row scales of X (slicing, product)
+  float sy[kMaxOrder], py[kMaxOrder];  // column scales of Y
+  float2 dx[kMaxM];                    // X[r][r mod K] (double-float), left out of the slices of X
+  unsigned colmax[kMaxOrder];
+  double red[kMaxWarps * 32];
+  uint64_t mma_bar[2];
+  uint32_t tmem;
+  int item;
+  int abort_flag;
 };
 
-// Block-wide ||A||_1 with FP64 accumulation: one thread per column.
-__device__ double block_norm1(const float* __restrict__ A, int n, double* red) {
+// Per-CTA progress of the two-stage pipeline: chunks issued so far.
+struct Pipe {
+  int chunks;
+};
+
+// Block-wide ||A||_1 of an FP32 matrix: FP64 column sums (warp w of W adds
+// rows w, w + W, ... of 32 columns, the W partial sums are added in a fixed
+// order), maximum by warp shuffles; NaN propagates.
+template <int kWarps>
+__device__ double block_norm1(const float* __restrict__ A, int n, Shared& sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double qnan = __longlong_as_double(0x7ff8000000000000ULL);
   double best = 0.0;
   bool nan = false;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    double sum = 0.0;
-    for (int r = 0; r < n; ++r) sum += fabs((double)A[(int64_t)r * n + c]);
-    if (isnan(sum)) nan = true;
-    best = fmax(best, sum);
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int c = c0 + lane;
+    double part = 0.0;
+    if (c < n)
+      for (int r = warp; r < n; r += kWarps) part += fabs((double)A[(int64_t)r * n + c]);
+    sh.red[warp * 32 + lane] = part;
+    __syncthreads();
+    if (warp == 0 && c < n) {
+      double col = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) col += sh.red[w * 32 + lane];
+      if (isnan(col)) nan = true;
+      best = fmax(best, col);
+    }
+    __syncthreads();
   }
-  if (nan) best = __longlong_as_double(0x7ff8000000000000ULL);
-  for (int off = 16; off > 0; off >>= 1) {
-    const double o = __shfl_xor_sync(0xffffffffu, best, off);
-    best = (isnan(best) || isnan(o)) ? __longlong_as_double(0x7ff8000000000000ULL) : fmax(best, o);
+  if (warp == 0) {
+    if (nan) best = qnan;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_xor_sync(0xffffffffu, best, off);
+      best = (isnan(best) || isnan(o)) ? qnan : fmax(best, o);
+    }
+    if (lane == 0) sh.red[0] = best;
   }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
   __syncthreads();
-  double r = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-    r = (isnan(r) || isnan(red[w])) ? __longlong_as_double(0x7ff8000000000000ULL) : fmax(r, red[w]);
+  const double r = sh.red[0];
   __syncthreads();
   return r;
 }
 
-// One CTA product P = X Y (M x N, inner K, leading dimension ld for every
-// matrix) in tiles of T x T; the epilogue is either a plan step (st != null)
-// or the stacked double-angle form (rows < split to outC as 2X - I, the rest
-// to outS as 2X).
-//
-// 256 threads as 16 x 16; thread (ty, tx) owns rows {ty*H + i, T/2 + ty*H + i}
-// and columns {tx*H + j, T/2 + tx*H + j}, H = T/32, so that its operands are
-// read from shared memory as float4 without bank conflicts.  The k-panels
-// (kBK deep) are double-buffered: the next panel is fetched from global
-// memory into registers while the current one is multiplied.
-template <int T>
-__device__ void cta_product(const float* __restrict__ X, const float* __restrict__ Y, int M, int N, int K, int ld,
-                            const DStep* st, const Slots& sl, float a2, float as, int split, float* outC,
-                            float* outS, float* smem) {
-  constexpr int H = T / 32;      // half micro-tile edge: 4 (T = 128) or 2 (T = 64)
-  constexpr int R = 2 * H;       // micro-tile edge
-  constexpr int LD = T + 4;      // shared-memory row pitch (floats)
-  constexpr int PER = (T * kBK) / kThreads;  // panel elements per thread per operand
-  float (*Xs)[kBK][LD] = reinterpret_cast<float (*)[kBK][LD]>(smem);           // [2][kBK][LD]
-  float (*Ys)[kBK][LD] = reinterpret_cast<float (*)[kBK][LD]>(smem + 2 * kBK * LD);
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const float* inp[EPI_MAX_IN];
-  float* outp[EPI_MAX_OUT];
-  float alph[EPI_MAX_OUT];
-  int nin = 0, nout = 0;
-  if (st) {
-    nin = st->nin;
-    nout = st->nout;
+// Row scales of X (M x K, each row without its entry X[r][r mod K], which
+// is kept apart) and column scales of Y (K x N) into shared memory.  Warps
+// take four rows (or a lane four k of its column) per round so that the
+// loads are in flight together.
+template <int kWarps>
+__device__ void prepass(const Opnd& X, const Opnd& Y, int M, int N, int K, int n, Shared& sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kR = 4;
+  for (int r0 = warp * kR; r0 < M; r0 += kWarps * kR) {
+    unsigned mx[kR];
 #pragma unroll
-    for (int q = 0; q < EPI_MAX_IN; ++q) inp[q] = q < nin ? sl.p[st->in[q]] : nullptr;
+    for (int i = 0; i < kR; ++i) mx[i] = 0u;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+      const int k = k0 + lane;
+      dfl v[kR];
 #pragma unroll
-    for (int t = 0; t < EPI_MAX_OUT; ++t) {
-      outp[t] = t < nout ? sl.p[st->out[t]] : nullptr;
-      alph[t] = st->scale[t] == 1 ? st->alpha[t] * a2 : st->scale[t] == 2 ? st->alpha[t] * as : st->alpha[t];
+      for (int i = 0; i < kR; ++i) v[i] = (r0 + i < M && k < K) ? opnd_get(X, r0 + i, k, n) : dfl{0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < kR; ++i) {
+        if (r0 + i >= M || k >= K) continue;
+        const int d = r0 + i >= K ? r0 + i - K : r0 + i;  // (r0 + i) mod K, M <= 2K
+        if (k == d) sh.dx[r0 + i] = make_float2(v[i].hi, v[i].lo);
+        else mx[i] = max(mx[i], __float_as_uint(fabsf(v[i].hi)));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      const unsigned m = __reduce_max_sync(0xffffffffu, mx[i]);
+      if (lane == 0 && r0 + i < M) scales_of(m, &sh.sx[r0 + i], &sh.px[r0 + i]);
     }
   }
-  for (int m0 = 0; m0 < M; m0 += T) {
-    for (int n0 = 0; n0 < N; n0 += T) {
-      float acc[R][R];
+  for (int c = threadIdx.x; c < N; c += kWarps * 32) sh.colmax[c] = 0u;
+  __syncthreads();
+  for (int c0 = 0; c0 < N; c0 += 32) {
+    const int c = c0 + lane;
+    unsigned mx = 0u;
+    for (int k0 = warp; k0 < K; k0 += kWarps * kR) {
+      float v[kR];
 #pragma unroll
-      for (int i = 0; i < R; ++i)
+      for (int i = 0; i < kR; ++i) {
+        const int k = k0 + i * kWarps;
+        v[i] = (c < N && k < K) ? Y.hi[(int64_t)k * n + c] : 0.f;
+      }
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc[i][j] = 0.f;
-      float xr[PER], yr[PER];
-#define CS_BT_FETCH(k0_)                                                     \
-  _Pragma("unroll") for (int t = 0; t < PER; ++t) {                          \
-    const int e = tid + t * kThreads;                                        \
-    const int mm = e / kBK, kk = e % kBK;                                    \
-    const int gm = m0 + mm, gk = (k0_) + kk;                                 \
-    xr[t] = (gm < M && gk < K) ? X[(int64_t)gm * ld + gk] : 0.f;             \
-    const int kk2 = e / T, nn = e % T;                                       \
-    const int gk2 = (k0_) + kk2, gn = n0 + nn;                               \
-    yr[t] = (gk2 < K && gn < N) ? Y[(int64_t)gk2 * ld + gn] : 0.f;           \
+      for (int i = 0; i < kR; ++i) mx = max(mx, __float_as_uint(fabsf(v[i])));
+    }
+    if (c < N) atomicMax(&sh.colmax[c], mx);
   }
-#define CS_BT_STASH(buf_)                                                    \
-  _Pragma("unroll") for (int t = 0; t < PER; ++t) {                          \
-    const int e = tid + t * kThreads;                                        \
-    Xs[(buf_)][e % kBK][e / kBK] = xr[t];                                    \
-    Ys[(buf_)][e / T][e % T] = yr[t];                                        \
+  __syncthreads();
+  for (int c = threadIdx.x; c < N; c += kWarps * 32) scales_of(sh.colmax[c], &sh.sy[c], &sh.py[c]);
+  __syncthreads();
+}
+
+// Slices of X rows [m0, m0 + 128) (without X[r][r mod K]) and Y columns
+// [n0, n0 + n16) for k in [k0, k0 + 32) into one stage.  Each
+// warp covers 8 x 8 blocks, a word (two k) per lane: the 32 words of a block
+// and slice fall on distinct banks.  A warp loads every element of its
+// blocks before it converts any, so the loads are in flight together.
+template <int NT>
+__device__ void slice_chunk(const Opnd& X, const Opnd& Y, int m0, int n0, int M, int N, int n16, int K, int k0,
+                            int n, const Shared& sh, uint8_t* stA, uint8_t* stB) {
+  using C = Cfg<NT>;
+  constexpr int kWarps = C::kWarps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kAB = (kBM / 8) * 4 / kWarps;  // A blocks per warp
+  {
+    dfl v[kAB][2];
+#pragma unroll
+    for (int i = 0; i < kAB; ++i) {
+      const int b = warp + i * kWarps;
+      const int r = m0 + (b >> 2) * 8 + (lane >> 2), k = k0 + (b & 3) * 8 + 2 * (lane & 3);
+      v[i][0] = v[i][1] = dfl{0.f, 0.f};
+      if (r < M) {
+        const int d = r >= K ? r - K : r;  // r mod K (M <= 2K)
+        if (k < K && k != d) v[i][0] = opnd_get(X, r, k, n);
+        if (k + 1 < K && k + 1 != d) v[i][1] = opnd_get(X, r, k + 1, n);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kAB; ++i) {
+      const int b = warp + i * kWarps;
+      const int rl = (b >> 2) * 8 + (lane >> 2), kk = (b & 3) * 8 + 2 * (lane & 3);
+      const float sc = m0 + rl < M ? sh.sx[m0 + rl] : 0.f;
+      float d0[kSlices], d1[kSlices];
+      digits(v[i][0], sc, d0);
+      digits(v[i][1], sc, d1);
+      const uint32_t off = swz64(rl, kk);
+#pragma unroll
+      for (int p = 0; p < kSlices; ++p)
+        *reinterpret_cast<uint32_t*>(stA + p * C::kABytes + off) = pack_bf16(d0[p], d1[p]);
+    }
   }
-      CS_BT_FETCH(0)
-      CS_BT_STASH(0)
-      __syncthreads();
-      int buf = 0;
-      for (int k0 = 0; k0 < K; k0 += kBK) {
-        const bool more = k0 + kBK < K;
-        if (more) {
-          CS_BT_FETCH(k0 + kBK)
-        }
+  const int nb = (n16 / 8) * 4;
+  for (int b0 = 0; b0 < nb; b0 += 4 * kWarps) {
+    dfl v[4][2];
 #pragma unroll
-        for (int kk = 0; kk < kBK; ++kk) {
-          float a[R], b[R];
+    for (int i = 0; i < 4; ++i) {
+      const int b = b0 + warp + i * kWarps;
+      const int c = n0 + (b >> 2) * 8 + (lane & 7), k = k0 + (b & 3) * 8 + 2 * (lane >> 3);
+      v[i][0] = v[i][1] = dfl{0.f, 0.f};
+      if (b < nb && c < N) {
+        if (k < K) v[i][0] = opnd_get(Y, k, c, n);
+        if (k + 1 < K) v[i][1] = opnd_get(Y, k + 1, c, n);
+      }
+    }
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+    for (int i = 0; i < 4; ++i) {
+      const int b = b0 + warp + i * kWarps;
+      if (b >= nb) break;
+      const int cl = (b >> 2) * 8 + (lane & 7), kk = (b & 3) * 8 + 2 * (lane >> 3);
+      const float sc = n0 + cl < N ? sh.sy[n0 + cl] : 0.f;
+      float d0[kSlices], d1[kSlices];
+      digits(v[i][0], sc, d0);
+      digits(v[i][1], sc, d1);
+      const uint32_t off = swz64(cl, kk);
 #pragma unroll
-            for (int q = 0; q < H; q += 4 > H ? H : 4) {
-              if (H >= 4) {
-                const float4 va = *reinterpret_cast<const float4*>(&Xs[buf][kk][h * (T / 2) + ty * H + q]);
-                const float4 vb = *reinterpret_cast<const float4*>(&Ys[buf][kk][h * (T / 2) + tx * H + q]);
-                a[h * H + q] = va.x; a[h * H + q + 1] = va.y; a[h * H + q + 2] = va.z; a[h * H + q + 3] = va.w;
-                b[h * H + q] = vb.x; b[h * H + q + 1] = vb.y; b[h * H + q + 2] = vb.z; b[h * H + q + 3] = vb.w;
-              } else {
-                const float2 va = *reinterpret_cast<const float2*>(&Xs[buf][kk][h * (T / 2) + ty * H]);
-                const float2 vb = *reinterpret_cast<const float2*>(&Ys[buf][kk][h * (T / 2) + tx * H]);
-                a[h * H] = va.x; a[h * H + 1] = va.y;
-                b[h * H] = vb.x; b[h * H + 1] = vb.y;
+      for (int q = 0; q < kSlices; ++q)
+        *reinterpret_cast<uint32_t*>(stB + q * C::kBBytes + off) = pack_bf16(d0[q], d1[q]);
+    }
+  }
+}
+
+// The per-matrix state the epilogues need.
+struct Mat {
+  const float* A;
+  float* C;  // caller's outputs (FP32)
+  float* S;
+  float* ws;  // the CTA's workspace slice
+  int n, s;
+  int64_t n2;
+  float a2, as;  // 4^-s, 2^-s
+};
+
+// Double-float slot k (W0..W7 = 0..7, C = 8, S = 9) of the workspace.
+__device__ __forceinline__ int df_index(int slot) { return slot == SL_C ? 8 : slot == SL_S ? 9 : slot - W(0); }
+__device__ __forceinline__ float* df_hi(const Mat& m, int slot) { return m.ws + 2 * (int64_t)df_index(slot) * m.n2; }
+
+// Which epilogue a product runs.
+struct Epi {
+  int f, k;      // chain step k of family f, or k < 0: double-angle step
+  float* outC;   // double-angle: rows < n -> 2P - I here, rows >= n -> 2P to outS
+  float* outS;
+};
+
+constexpr int kEpiBatch = 4;  // entries a thread finishes at once
+
+// Finishes kEpiBatch entries (r[i], c[i]) of a product: the left-out
+// diagonal term X[r][d] Y[d][c] (d = r mod n) is added to the slice product,
+// then the step's epilogue runs (terms whose coefficient is zero are
+// skipped; the branches are uniform).  Every load is issued before the
+// arithmetic that uses it.
+__device__ __forceinline__ void finish(const Opnd& Y, const Mat& m, const Epi& ep, const Shared& sh,
+                                       const int (&r)[kEpiBatch], const int (&c)[kEpiBatch], dfl (&P)[kEpiBatch],
+                                       const bool (&ok)[kEpiBatch]) {
+  const int n = m.n;
+  const bool chain = ep.k >= 0;
+  const DStep& st = c_plans[chain ? ep.f : 0].step[chain ? ep.k : 0];
+  const int nin = chain ? st.nin : 0;
+  dfl ydc[kEpiBatch], in[kEpiBatch][kMaxIn];
+#pragma unroll
+  for (int i = 0; i < kEpiBatch; ++i) {
+    ydc[i] = dfl{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < kMaxIn; ++q) in[i][q] = dfl{0.f, 0.f};
+    if (!ok[i]) continue;
+    const int d = r[i] >= n ? r[i] - n : r[i];
+    ydc[i] = opnd_get(Y, d, c[i], n);
+    const int idx = r[i] * n + c[i];
+#pragma unroll
+    for (int q = 0; q < kMaxIn; ++q) {
+      if (q < nin) {
+        const float* h = df_hi(m, st.in[q]);
+        in[i][q] = dfl{h[idx], h[idx + m.n2]};
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kEpiBatch; ++i) {
+    if (!ok[i]) continue;
+    dfl p = P[i];
+    df_acc(p, df_mul_raw(sh.dx[r[i]], ydc[i]));
+    p = fast_two_sum(p.hi, p.lo);
+    const int idx = r[i] * n + c[i];
+    if (!chain) {
+      const float v = 2.f * (p.hi + p.lo);
+      if (r[i] < n) ep.outC[idx] = v - (r[i] == c[i] ? 1.f : 0.f);
+      else ep.outS[idx - (int)m.n2] = v;
+      continue;
+    }
+    dfl o0 = dfl{0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < EPI_MAX_OUT; ++t) {
+      if (t < st.nout) {
+        float2 al = st.alpha[t];
+        const float sc = st.scale[t] == 1 ? m.a2 : st.scale[t] == 2 ? m.as : 1.f;
+        al.x *= sc;
+        al.y *= sc;
+        dfl v = df_mul_raw(al, p);
+        if (r[i] == c[i] && st.gamma[t].x != 0.f) df_acc(v, dfl{st.gamma[t].x, st.gamma[t].y});
+#pragma unroll
+        for (int q = 0; q < kMaxIn; ++q)
+          if (q < nin && st.beta[t][q].x != 0.f) df_acc(v, df_mul_raw(st.beta[t][q], in[i][q]));
+        if (t > 0 && st.delta[t].x != 0.f) df_acc(v, df_mul_raw(st.delta[t], o0));
+        v = fast_two_sum(v.hi, v.lo);
+        if (t == 0) o0 = v;
+        const int slot = st.out[t];
+        float* h = df_hi(m, slot);
+        h[idx] = v.hi;
+        h[idx + m.n2] = v.lo;
+        if (m.s == 0 && (slot == SL_C || slot == SL_S)) (slot == SL_C ? m.C : m.S)[idx] = v.hi + v.lo;
+      }
+    }
+  }
+}
+
+// One product P = X Y (M x N, inner K = n) of matrix m with its epilogue.
+template <int NT>
+__device__ bool product(const Opnd& X, const Opnd& Y, int M, int N, int K, const Mat& m, const Epi& ep,
+                        Shared& sh, uint8_t* smem, Pipe& pipe) {
+  using C = Cfg<NT>;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = m.n;
+  prepass<C::kWarps>(X, Y, M, N, K, n, sh);
+  const int nchunks = (K + kKc - 1) / kKc;
+  for (int m0 = 0; m0 < M; m0 += kBM) {
+    for (int n0 = 0; n0 < N; n0 += NT) {
+      const int ntile = min(NT, N - n0);
+      const int n16 = (ntile + 15) & ~15;
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n16 >> 3) << 17) |
+                             ((uint32_t)(kBM >> 4) << 24);
+      for (int kc = 0; kc < nchunks; ++kc) {
+        const int g = pipe.chunks;
+        const int st = g & 1;
+        // the stage was last read by chunk g - 2
+        if (g >= 2 && !mbar_wait(&sh.mma_bar[st], ((g - 2) >> 1) & 1, (volatile int*)&sh.abort_flag))
+          sh.abort_flag = 1;
+        __syncthreads();
+        if (sh.abort_flag) return false;
+        uint8_t* stA = smem + st * C::kStageBytes;
+        uint8_t* stB = stA + kSlices * C::kABytes;
+        slice_chunk<NT>(X, Y, m0, n0, M, N, n16, K, kc * kKc, n, sh, stA, stB);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          // descriptors: start address >> 4, LBO 1 (unused), SBO 512 bytes
+          // (8 rows of 64 bytes), version 1, 64-byte swizzle
+          constexpr uint32_t kDescHi = (512u >> 4) | (1u << 14) | (4u << 29);
+          const uint32_t a_lo = ((smem_u32(stA) & 0x3FFFFu) >> 4) | (1u << 16);
+          const uint32_t b_lo = ((smem_u32(stB) & 0x3FFFFu) >> 4) | (1u << 16);
+#pragma unroll
+          for (int j = 0; j < kKc / 16; ++j) {
+            if (kc * kKc + 16 * j >= K) break;
+            const bool first = kc == 0 && j == 0;
+#pragma unroll
+            for (int p = 0; p < kSlices; ++p) {
+              const uint64_t ad = ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * C::kABytes + 32 * j) >> 4));
+#pragma unroll
+              for (int q = 0; p + q < kSlices; ++q) {
+                const uint64_t bd =
+                    ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * C::kBBytes + 32 * j) >> 4));
+                // p = 0 reaches every level first: it restarts the accumulators
+                mma_bf16(sh.tmem + (uint32_t)((p + q) * NT), ad, bd, idesc, (first && p == 0) ? 0u : 1u);
               }
             }
           }
-#pragma unroll
-          for (int i = 0; i < R; ++i)
-#pragma unroll
-            for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          mma_commit(&sh.mma_bar[st]);
         }
-        if (more) {
-          CS_BT_STASH(buf ^ 1)
-          __syncthreads();
-          buf ^= 1;
+        pipe.chunks = g + 1;
+      }
+      // every MMA of the tile has completed once the last chunk's commit has;
+      // the stages are then free, and the epilogue stages through them
+      {
+        const int g = pipe.chunks - 1;
+        if (!mbar_wait(&sh.mma_bar[g & 1], (g >> 1) & 1, (volatile int*)&sh.abort_flag)) sh.abort_flag = 1;
+        __syncthreads();
+        if (sh.abort_flag) return false;
+        tc_fence_after();
+      }
+      // Epilogue.  Warp w drains TMEM lanes 32 (w & 3).. and its span of
+      // columns in groups of 16, combines the levels and stages the
+      // tile's P (hi and lo planes of 128 x NT floats, column index XOR-ed
+      // with the row's low 5 bits, so that both the drain, lane = row, and
+      // the walk, thread = column, are conflict-free) in the idle stages;
+      // then every thread finishes entries of the tile, row by row.
+      {
+        constexpr int kSpan = NT / (C::kWarps / 4);  // columns per warp
+        const int quarter = warp & 3;
+        const int cbase = (warp >> 2) * kSpan;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        float* t_hi = reinterpret_cast<float*>(smem);
+        float* t_lo = t_hi + kBM * NT;
+        const int rl = quarter * 32 + lane;
+        const float pr = m0 + rl < M ? sh.px[m0 + rl] : 0.f;
+        for (int g16 = 0; g16 < kSpan; g16 += 16) {
+          const int cl0 = cbase + g16;
+          if (cl0 >= ntile) break;  // uniform over the warp
+          uint32_t v[kSlices][16];
+#pragma unroll
+          for (int L = 0; L < kSlices; ++L) tmem_ld16(sh.tmem + lane_off + (uint32_t)(L * NT + cl0), v[L]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = n0 + cl0 + j;
+            const float sc = pr * (c < N ? sh.py[c] : 0.f);
+            const float l0 = __uint_as_float(v[0][j]), l1 = __uint_as_float(v[1][j]);
+            const float l2 = __uint_as_float(v[2][j]), l3 = __uint_as_float(v[3][j]);
+            dfl P = two_sum(l0, l1 * 0x1p-7f);
+            P = fast_two_sum(P.hi, P.lo + (l2 * 0x1p-14f + l3 * 0x1p-21f));
+            const int a = rl * NT + ((cl0 + j) ^ (rl & 31));
+            t_hi[a] = P.hi * sc;
+            t_lo[a] = P.lo * sc;
+          }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // rows of the tile round-robin over the warps, lanes along columns:
+        // kEpiBatch entries per thread, NT / 32 columns x kRows rows
+        const int mrows = min(kBM, M - m0);
+        constexpr int kCols = NT / 32, kRows = kEpiBatch / kCols;
+        for (int rt0 = warp * kRows; rt0 < mrows; rt0 += C::kWarps * kRows) {
+          int r[kEpiBatch], c[kEpiBatch];
+          bool ok[kEpiBatch];
+          dfl P[kEpiBatch];
+#pragma unroll
+          for (int i = 0; i < kEpiBatch; ++i) {
+            const int rt = rt0 + i / kCols, ct = lane + 32 * (i % kCols);
+            ok[i] = rt < mrows && ct < ntile;
+            r[i] = m0 + rt;
+            c[i] = n0 + ct;
+            const int a = (rt & (kBM - 1)) * NT + (ct ^ (rt & 31));
+            P[i] = ok[i] ? dfl{t_hi[a], t_lo[a]} : dfl{0.f, 0.f};
+          }
+          finish(Y, m, ep, sh, r, c, P, ok);
         }
       }
-#pragma unroll
-      for (int i = 0; i < R; ++i) {  // unrolled: acc[i][j] stays in registers
-        const int r = m0 + (i < H ? ty * H + i : T / 2 + ty * H + (i - H));
-        if (r >= M) continue;
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int c = n0 + (j < H ? tx * H + j : T / 2 + tx * H + (j - H));
-          if (c >= N) continue;
-          const float p = acc[i][j];
-          if (!st) {
-            if (r < split) outC[(int64_t)r * ld + c] = 2.f * p - (r == c ? 1.f : 0.f);
-            else outS[(int64_t)(r - split) * ld + c] = 2.f * p;
-            continue;
-          }
-          const int64_t idx = (int64_t)r * ld + c;
-          float in[EPI_MAX_IN], o[EPI_MAX_OUT];
-#pragma unroll
-          for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < nin ? inp[q][idx] : 0.f;
-#pragma unroll
-          for (int t = 0; t < EPI_MAX_OUT; ++t) {
-            if (t >= nout) break;
-            float v = alph[t] * p + (r == c ? st->gamma[t] : 0.f);
-#pragma unroll
-            for (int q = 0; q < EPI_MAX_IN; ++q)
-              if (q < nin) v = fmaf(st->beta[t][q], in[q], v);
-#pragma unroll
-            for (int u = 0; u < t; ++u) v = fmaf(st->delta[t][u], o[u], v);
-            o[t] = v;
-          }
-#pragma unroll
-          for (int t = 0; t < EPI_MAX_OUT; ++t)
-            if (t < nout) outp[t][idx] = o[t];
-        }
-      }
-      __syncthreads();  // the next tile overwrites both panel buffers
+      // the next tile's slices overwrite the staged tile, and the next
+      // product reads what this one wrote
+      tc_fence_before();
+      __syncthreads();
     }
   }
-#undef CS_BT_FETCH
-#undef CS_BT_STASH
+  return true;
 }
 
-// T is the tile edge for orders above 64; orders <= 64 always use 64-wide tiles.
-template <int T, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order,
-                                                           int count, int* queue, float* ws_all, int64_t ws_per_cta,
-                                                           cs_info* infos, int32_t* status) {
-  __shared__ __align__(16) float panels[4 * kBK * (T + 4)];
-  __shared__ double red[kThreads / 32];
-  __shared__ int item;
+template <int NT>
+__global__ void __launch_bounds__(Cfg<NT>::kThreads, Cfg<NT>::kCtasPerSm)
+    batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order, int count, int* queue,
+                   float* ws_all, int64_t ws_per_cta, cs_info* infos, int32_t* status, int* err) {
+  using C = Cfg<NT>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ Shared sh;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.mma_bar[0], 1);
+    mbar_init(&sh.mma_bar[1], 1);
+    sh.abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&sh.tmem, C::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  Pipe pipe{0};
   float* ws = ws_all + (int64_t)blockIdx.x * ws_per_cta;
   for (;;) {
-    if (threadIdx.x == 0) item = atomicAdd(queue, 1);
+    if (threadIdx.x == 0) sh.item = atomicAdd(queue, 1);
     __syncthreads();
-    const int i = item;
+    const int i = sh.item;
     __syncthreads();
-    if (i >= count) break;
+    if (i >= count || sh.abort_flag) break;
     const int j = order[i];
     const Desc d = desc[j];
     const int n = (int)d.n;
@@ -257,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batched_kernel(const Desc* __r
       }
       continue;
     }
-    const double nrm = block_norm1(d.A, n, red);
+    const double nrm = block_norm1<C::kWarps>(d.A, n, sh);
     int f = 0, s = 0;
     const int sel = select_family(nrm, 1, &f, &s);
     if (threadIdx.x == 0) {
@@ -277,50 +699,88 @@ __global__ void __launch_bounds__(kThreads, MINB) batched_kernel(const Desc* __r
       __syncthreads();
       continue;
     }
-    const int64_t n2 = (int64_t)n * n;
-    float* ping0 = ws + 8 * n2;
-    float* ping1 = ws + 10 * n2;
-    Slots sl;
-    sl.p[SL_A] = const_cast<float*>(d.A);
-    sl.p[SL_C] = s == 0 ? d.C : ping0;
-    sl.p[SL_S] = s == 0 ? d.S : ping0 + n2;
-    for (int w = 0; w < kWorkSlots; ++w) sl.p[W(w)] = ws + w * n2;
-    const float a2 = ldexpf(1.f, -2 * s), as = ldexpf(1.f, -s);
+    Mat m;
+    m.A = d.A;
+    m.C = d.C;
+    m.S = d.S;
+    m.ws = ws;
+    m.n = n;
+    m.s = s;
+    m.n2 = (int64_t)n * n;
+    m.a2 = ldexpf(1.f, -2 * s);
+    m.as = ldexpf(1.f, -s);
+    auto slot_opnd = [&](int slot) {
+      if (slot == SL_A) return Opnd{d.A, nullptr, nullptr, nullptr, n};
+      const float* h = df_hi(m, slot);
+      return Opnd{h, h + m.n2, nullptr, nullptr, n};
+    };
+    bool ok = true;
     const DPlan& P = c_plans[f];
-    for (int k = 0; k < P.nsteps; ++k) {
-      const DStep* st = &P.step[k];
-      if (T == 128 && n > 64)
-        cta_product<128>(sl.p[st->X], sl.p[st->Y], n, n, n, n, st, sl, a2, as, 0, nullptr, nullptr, panels);
-      else
-        cta_product<64>(sl.p[st->X], sl.p[st->Y], n, n, n, n, st, sl, a2, as, 0, nullptr, nullptr, panels);
+    for (int k = 0; k < P.nsteps && ok; ++k) {
+      const Opnd X = slot_opnd(P.step[k].X), Y = slot_opnd(P.step[k].Y);
+      ok = product<NT>(X, Y, n, n, n, m, Epi{f, k, nullptr, nullptr}, sh, smem, pipe);
     }
-    for (int q = 0; q < s; ++q) {
-      float* cur = (q & 1) ? ping1 : ping0;
-      float* nxt = (q & 1) ? ping0 : ping1;
+    // double-angle steps: the first reads the chain's double-float C and S,
+    // the others the FP32 stacked buffers ping[0], ping[1]
+    float* ping0 = ws + (int64_t)2 * kDfSlots * m.n2;
+    float* ping1 = ping0 + 2 * m.n2;
+    for (int q = 0; q < s && ok; ++q) {
+      Opnd X, Y;
+      if (q == 0) {
+        const float* ch = df_hi(m, SL_C);
+        const float* sh_ = df_hi(m, SL_S);
+        X = Opnd{ch, ch + m.n2, sh_, sh_ + m.n2, n};
+        Y = Opnd{ch, ch + m.n2, nullptr, nullptr, n};
+      } else {
+        const float* cur = (q & 1) ? ping0 : ping1;
+        X = Opnd{cur, nullptr, cur + m.n2, nullptr, n};
+        Y = Opnd{cur, nullptr, nullptr, nullptr, n};
+      }
+      float* nxt = (q & 1) ? ping1 : ping0;
       const bool last = q == s - 1;
-      if (T == 128 && n > 64)
-        cta_product<128>(cur, cur, 2 * n, n, n, n, nullptr, sl, 0.f, 0.f, n, last ? d.C : nxt,
-                         last ? d.S : nxt + n2, panels);
-      else
-        cta_product<64>(cur, cur, 2 * n, n, n, n, nullptr, sl, 0.f, 0.f, n, last ? d.C : nxt,
-                        last ? d.S : nxt + n2, panels);
+      ok = product<NT>(X, Y, 2 * n, n, n, m, Epi{0, -1, last ? d.C : nxt, last ? d.S : nxt + m.n2}, sh, smem, pipe);
     }
+    if (!ok) break;
+  }
+  // Teardown: after an expired wait, wait (bounded) for the MMAs this CTA
+  // issued before freeing TMEM, and raise the error word.
+  __syncthreads();
+  if (sh.abort_flag && threadIdx.x == 0) {
+    if (pipe.chunks > 0) {
+      volatile int never = 0;
+      const int g = pipe.chunks - 1;
+      mbar_wait(&sh.mma_bar[g & 1], (g >> 1) & 1, &never);
+    }
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(sh.tmem, C::kTmemCols);
   }
 }
 
 // ------------------------------------------------------------------- host ---
 struct Variant {
-  int tile;
+  int tile;  // output tile columns (N of each MMA, at most)
   int ctas_per_sm;
 };
-// {64, 4} compiles with 64 registers per thread to fit 32 warps per SM; the
-// autotuner keeps whichever variant is fastest on the batch.  (A 128-wide
-// tile at 2 CTAs per SM would spill 3 KB per thread.)
-const Variant kVariants[] = {{128, 1}, {64, 2}, {64, 1}, {64, 4}};
+// Tiles of 128 x 128 (four level accumulators fill TMEM's 512 columns, one
+// CTA per SM) or 128 x 64 (half of TMEM, two CTAs per SM, so one CTA's
+// slicing and epilogue overlap the other's MMAs; orders above 64 take twice
+// the tiles): the autotuner keeps whichever is faster on the batch.
+const Variant kVariants[] = {{128, 1}, {64, 2}};
 
 std::mutex g_mu;
 bool g_plans_uploaded[64] = {};
 std::map<std::string, int> g_tuned;  // batch signature -> variant index
+
+// A coefficient as a double-float pair (hi, lo), hi + lo = c to about 2^-48.
+float2 df_pair(double c) {
+  const float h = (float)c;
+  return make_float2(h, (float)(c - (double)h));
+}
 
 cs_status upload_plans() {
   int dev = 0;
@@ -343,20 +803,25 @@ cs_status upload_plans() {
       for (int t = 0; t < D.nout; ++t) {
         const OutSpec& o = steps[k].outs[t];
         D.out[t] = o.slot;
-        D.alpha[t] = (float)o.alpha;
-        D.gamma[t] = (float)o.gamma;
+        D.alpha[t] = df_pair(o.alpha);
+        D.gamma[t] = df_pair(o.gamma);
         D.scale[t] = (k == 0) ? 1 : (o.slot == SL_S ? 2 : 0);
         for (auto& b : o.beta) {
+          if (b.first == SL_A) return fail(CS_EINVAL, "batched plans read A only as a product operand");
           int q = -1;
           for (int z = 0; z < D.nin; ++z)
             if (D.in[z] == b.first) q = z;
           if (q < 0) {
+            if (D.nin == kMaxIn) return fail(CS_EINVAL, "batched plans read at most four matrices per product");
             q = D.nin++;
             D.in[q] = b.first;
           }
-          D.beta[t][q] = (float)b.second;
+          D.beta[t][q] = df_pair(b.second);
         }
-        for (auto& d : o.delta) D.delta[t][d.first] = (float)d.second;
+        for (auto& d : o.delta) {
+          if (d.first != 0 || t == 0) return fail(CS_EINVAL, "batched plans chain outputs only to the first output");
+          D.delta[t] = df_pair(d.second);
+        }
       }
     }
   }
@@ -388,31 +853,35 @@ BLayout make_blayout(int64_t count, int64_t nmax) {
   off += al(sizeof(int) * (size_t)std::max<int64_t>(count, 1));
   L.queue = off;
   off += 256;
-  L.per_cta = kSlots * nmax * nmax;
-  L.max_ctas = sm_count() * 4;
+  L.per_cta = kFloatsPerN2 * nmax * nmax;
+  L.max_ctas = sm_count() * 2;
   L.scratch = off;
   off += al(sizeof(float) * (size_t)L.per_cta * L.max_ctas);
   L.total = off;
   return L;
 }
 
+template <int NT>
+cs_status launch_tile(int grid, const BLayout& L, char* ws, int count, cs_info* infos, int32_t* status, int* err,
+                      cudaStream_t stream) {
+  static std::atomic<unsigned long long> smem_set{0};
+  CS_CHECK(smem_limit_once(batched_kernel<NT>, Cfg<NT>::kSmem, smem_set));
+  batched_kernel<NT><<<grid, Cfg<NT>::kThreads, Cfg<NT>::kSmem, stream>>>(
+      (const Desc*)(ws + L.desc), (const int*)(ws + L.order), count, (int*)(ws + L.queue),
+      (float*)(ws + L.scratch), L.per_cta, infos, status, err);
+  CS_CUDA_CHECK(cudaGetLastError());
+  return CS_OK;
+}
+
 cs_status launch_variant(int v, const BLayout& L, char* ws, int count, cs_info* infos, int32_t* status,
                          cudaStream_t stream) {
   const Variant& V = kVariants[v];
   const int grid = std::min(L.max_ctas, sm_count() * V.ctas_per_sm);
-  int* queue = (int*)(ws + L.queue);
-  CS_CUDA_CHECK(cudaMemsetAsync(queue, 0, sizeof(int), stream));
-  const Desc* desc = (const Desc*)(ws + L.desc);
-  const int* order = (const int*)(ws + L.order);
-  float* scratch = (float*)(ws + L.scratch);
-  if (V.tile == 128)
-    batched_kernel<128, 1><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
-  else if (V.ctas_per_sm >= 4)
-    batched_kernel<64, 4><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
-  else
-    batched_kernel<64, 2><<<grid, kThreads, 0, stream>>>(desc, order, count, queue, scratch, L.per_cta, infos, status);
-  CS_CUDA_CHECK(cudaGetLastError());
-  return CS_OK;
+  int* err = tc_error_word();
+  if (!err) return fail(CS_ECUDA, "cannot resolve the device error word");
+  CS_CUDA_CHECK(cudaMemsetAsync(ws + L.queue, 0, sizeof(int), stream));
+  if (V.tile == 128) return launch_tile<128>(grid, L, ws, count, infos, status, err, stream);
+  return launch_tile<64>(grid, L, ws, count, infos, status, err, stream);
 }
 
 }  // namespace bt

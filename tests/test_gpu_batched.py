@@ -77,6 +77,24 @@ def test_every_order_and_family():
         check_against_oracle(mats[k], plan.C[k].cpu().numpy(), plan.S[k].cpu().numpy(), infos[k])
 
 
+def test_order_norm_grid():
+    """Orders {1, 5, 33, 64, 129, 192, 256} x ||A||_1 {8, 30, 64}, normal and
+    symmetric: every FP32-class result within 2e-5 of the oracle."""
+    mats = []
+    for fam in ("normal", "symmetric"):
+        for n in (1, 5, 33, 64, 129, 192, 256):
+            for nrm in (8.0, 30.0, 64.0):
+                mats.append(inputs.matrix(n, fam, nrm, index=86, sub=n).astype(np.float32))
+    dev = [torch.from_numpy(M).cuda() for M in mats]
+    plan = api.BatchedPlan(dev, autotune=False)
+    plan.launch()
+    torch.cuda.synchronize()
+    infos = plan.infos()
+    assert np.all(plan.status() == 0)
+    for k in range(len(mats)):
+        check_against_oracle(mats[k], plan.C[k].cpu().numpy(), plan.S[k].cpu().numpy(), infos[k])
+
+
 def test_replay_recomputes_and_is_deterministic():
     mats, dev = make_batch(30, index=83)
     plan = api.BatchedPlan(dev, autotune=False)
@@ -126,7 +144,8 @@ def test_full_workload_sampled():
     ns, norms, fams = inputs.batch_shapes(count, index=3)
     g = inputs.rng(3, 99)
     flat = []
-    sample = set(np.argsort(-ns)[:4]) | set(np.argsort(ns)[:4]) | set(g.choice(count, 24, replace=False))
+    sample = (set(np.argsort(-ns)[:4]) | set(np.argsort(ns)[:4]) | set(np.argsort(-norms)[:8])
+              | set(g.choice(count, 24, replace=False)))
     mats_np = {}
     for i in range(count):
         M = inputs.matrix(int(ns[i]), str(fams[i]), float(norms[i]), index=3, sub=i + 1).astype(np.float32)
