@@ -7,7 +7,10 @@ the FP64 path (double table) and, where built, the FP32 path (single table).
 Every matrix is an independent problem, so with N GPUs every rank runs the
 whole set (weak scaling, no collective on the data path).
 
-Prints one JSON line (see the repository's DESIGN notes for the fields).
+Prints one JSON line: the device-timed throughput, the same metric end to
+end through the public API with host buffers, the dominant kernel's
+roofline, the oracle on the host cores, and the other forms (precisions,
+batched, adjoint, c/s) with their errors.
 """
 from __future__ import annotations
 
@@ -123,39 +126,48 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def cpu_baseline(seconds_target=15.0):
-    """The oracle as it stands, on the host cores, on a bounded sample: FP64
-    n = 1024 N(0,1) matrices at ||A||_1 = 8 (2m = 24, s = 3: 13 products)."""
+def cpu_baseline(gpu_results=None):
+    """The oracle as it stands, on the host cores, on one matrix of the
+    headline workload: the n = 4096 N(0,1) FP64 matrix at ||A||_1 = 2^-4
+    (double table: 2m = 8, s = 0, 4 products, 0.55 TFLOP), about half a
+    minute on 16 cores.  With the GPU results of that matrix (FP64 and FP32
+    paths) their relative Frobenius error against this oracle result is
+    returned beside the timing (the FP32 path's against the double-table
+    oracle, i.e. against the function, at its own single-table (m, s))."""
     import oracle
-    from paper_2010_00465_gb300 import inputs
     oracle.build()
-    n = 1024
-    A = inputs.matrix(n, "normal", 8.0, index=1)
+    A = make_input("normal", 2.0 ** -4, "fp64")
     t0 = time.perf_counter()
-    done = 0
-    flops = 0.0
-    while True:
-        _, _, info = oracle.cossin(A)
-        done += 1
-        flops += 2.0 * n ** 3 * info["products"]
-        if time.perf_counter() - t0 >= seconds_target or done >= 3:
-            break
+    Co, So, info = oracle.cossin(A)
     dt = time.perf_counter() - t0
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d x oracle cos/sin of one n=%d FP64 N(0,1) matrix, ||A||_1=8 (2m=24, s=3), %.1f s"
-                      % (done, n, dt),
-            "matrices_per_s": done / dt}
+    flops = 2.0 * N ** 3 * info["products"]
+    out = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+           "sample": "one oracle cos/sin of the n=%d FP64 N(0,1) matrix at ||A||_1=2^-4 of the headline workload "
+                     "((2m, s) = (%d, %d), %d products), %.1f s" % (N, info["m"], info["s"], info["products"], dt),
+           "matrices_per_s": 1.0 / dt}
+    errs = {}
+    for prec, (C, S) in (gpu_results or {}).items():
+        Cg = C.double().cpu().numpy()
+        Sg = S.double().cpu().numpy()
+        errs[prec] = max(float(np.linalg.norm(Cg - Co) / np.linalg.norm(Co)),
+                         float(np.linalg.norm(Sg - So) / np.linalg.norm(So)))
+    out["gpu_rel_err_vs_this_oracle_result"] = errs
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper's method as a plain FP64 CPU
+    program), on the host cores, one n = 2048 N(0,1) FP64 matrix at
+    ||A||_1 = 2^-4 per step (the headline workload's family and norm at a
+    quarter of its size, 4 products, a few seconds a step)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     from paper_2010_00465_gb300 import inputs
     oracle.build()
-    n = 512
-    A = inputs.matrix(n, "normal", 8.0, index=1)
+    n = 2048
+    A = inputs.matrix(n, "normal", 2.0 ** -4, index=1)
     for _ in range(args.warmup):
         oracle.cossin(A)
     times, flops = [], 0.0
@@ -166,12 +178,13 @@ def run_reference(args):
         flops += 2.0 * n ** 3 * info["products"]
     total = sum(times)
     val = flops / total / 1e12
+    sample = "one oracle cos/sin of a 2048x2048 FP64 N(0,1) matrix, ||A||_1=2^-4, per step"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "n=512 FP64 ||A||_1=8 per step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": "one oracle cos/sin of a 512x512 FP64 N(0,1) matrix, ||A||_1=8, per step"},
+                             "sample": sample},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -237,8 +250,7 @@ def main():
     step(record=True)
     torch.cuda.synchronize()
     flops_per_step = sum(i["flops"] for i in infos)
-    launches_per_step = sum(2 + i["products"] + (0 if p == "fp64" else extra_launches(p, i))
-                            for (p, _, _), i in zip(work, infos))
+    launches_per_step = sum(launches_of(p, i) for (p, _, _), i in zip(work, infos))
 
     api.prof_reset()
     api.prof_enable(True)
@@ -256,12 +268,13 @@ def main():
         if ws > 1:
             dist.barrier()
     api.prof_enable(False)
+    api.device_status()  # no bounded wait of a tensor-core kernel expired in the timed region
     ms = ev0.elapsed_time(ev1)
     if ws > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    kern = {k: api.prof_read(k) for k in ("norm1", "gemm_f64", "gemm_tf32", "other")}
+    kern = {k: api.prof_read(k) for k in ("norm1", "gemm_f64", "gemm_tf32", "gemm_emu", "other")}
 
     # end to end through the public API with host buffers (pinned), copies inside
     host_in = [torch.from_numpy(make_input(f, r, p)).pin_memory() for p, f, r in work]
@@ -318,11 +331,11 @@ def main():
 
     total_flops = flops_per_step * args.steps * ws
     value = total_flops / (ms / 1e3) / 1e12
-    dominant = max(("gemm_f64", "gemm_tf32"), key=lambda k: kern[k][0])
+    dominant = max(("gemm_f64", "gemm_emu"), key=lambda k: kern[k][0])
     clocks = clk.summary()
     pk, pk_kind = peaks()
     roof = roofline(dominant, *kern[dominant], pk, pk_kind, clocks)
-    other = "gemm_tf32" if dominant == "gemm_f64" else "gemm_f64"
+    other = "gemm_emu" if dominant == "gemm_f64" else "gemm_f64"
     roof_other = roofline(other, *kern[other], pk, pk_kind, clocks)
     norm_ms, norm_n, norm_bytes = kern["norm1"]
     roof_norm = None
@@ -334,7 +347,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "+".join("f64" if p == "fp64" else "f32(4xtf32)" for p in precs),
+        "scaling": "weak", "vs_baseline": None, "dtype": "+".join("f64" if p == "fp64" else "f32" for p in precs),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "precisions": precs, "matrices_per_step": len(work),
                    "l2": "inputs > L2: each step reads %d matrices of %d MB and streams GBs of workspace"
@@ -357,7 +370,9 @@ def main():
     if rank == 0 and not args.no_forms:
         line["forms"] = forms(api, wsp)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        head = {p: o for (p, f, r), o in zip(work, outs) if f == "normal" and r == 2.0 ** -4}
+        line["cpu_baseline"] = cpu_baseline(head)
+        line["accuracy"]["n4096_norm2^-4_rel_err_vs_oracle"] = line["cpu_baseline"]["gpu_rel_err_vs_this_oracle_result"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -518,12 +533,12 @@ def adjoint_form(api, count=512, n=128, reps=3):
     return out
 
 
-def batched_form(api, count=20000, reps=5, fp64_sample=240):
+def batched_form(api, count=20000, reps=5):
     """The batched workload: 20,000 FP32 matrices, n log-uniform in [8, 256],
     ||A||_1 log-uniform in [2^-6, 2^6], half symmetric, in one graph-captured
     persistent launch (autotuned).  Against it: the plain FP64 GPU path, one
-    cossin call per matrix, timed on a random sample and scaled by the
-    sample's share of the batch's algorithmic flops."""
+    cossin call per matrix over the whole batch (each call's 1-norm read is a
+    host round trip), timed end to end."""
     import torch
     import oracle
     from paper_2010_00465_gb300 import inputs
@@ -542,43 +557,54 @@ def batched_form(api, count=20000, reps=5, fp64_sample=240):
         plan.launch()
     e1.record()
     torch.cuda.synchronize()
+    api.device_status()
+    assert np.all(plan.status() == 0)
     ms = e0.elapsed_time(e1) / reps
     infos = plan.infos()
     flops = float(infos["flops"].sum())
-    # accuracy: a few matrices against the oracle (single table, same (m, s))
+    # accuracy: the largest orders, the largest norms and a random set
+    # against the oracle (single table, same (m, s))
     g = inputs.rng(3, 77)
     errs = []
-    for i in list(np.argsort(-ns)[:2]) + list(g.choice(count, 6, replace=False)):
+    sample = list(np.argsort(-ns)[:2]) + list(np.argsort(-norms)[:3]) + list(g.choice(count, 6, replace=False))
+    for i in sample:
         A = host[i].astype(np.float64)
         Co, So, _ = oracle.cossin(A, "single", m=int(infos[i]["m"]), s=int(infos[i]["s"]))
         C = plan.C[i].double().cpu().numpy()
         S = plan.S[i].double().cpu().numpy()
         errs.append(max(float(np.linalg.norm(C - Co) / np.linalg.norm(Co)),
                         float(np.linalg.norm(S - So) / max(np.linalg.norm(So), 1e-300))))
-    # plain FP64 GPU path on a sample
-    idx = g.choice(count, fp64_sample, replace=False)
-    d64 = [torch.from_numpy(host[i].astype(np.float64)).cuda() for i in idx]
-    for A in d64[:4]:
-        api.cossin(A, "fp64")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    f64_flops = 0.0
-    for A in d64:
-        _, _, inf = api.cossin(A, "fp64", return_info=True)
-        f64_flops += inf["flops"]
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t0
-    est64_ms = 1e3 * t64 * (flops / max(f64_flops, 1.0))
     variant = plan.variant()
     plan.close()
+    # the plain FP64 GPU path on every matrix of the batch
+    d64 = [torch.from_numpy(M.astype(np.float64)).cuda() for M in host]
+    nmax = int(max(ns))
+    flat = torch.empty(2 * nmax * nmax, dtype=torch.float64, device="cuda")
+    wsf = torch.empty(api.workspace_size(nmax, "fp64"), dtype=torch.uint8, device="cuda")
+
+    def plain(A):
+        n = A.shape[0]
+        api.cossin(A, "fp64", workspace=wsf, out=(flat[: n * n].view(n, n), flat[n * n: 2 * n * n].view(n, n)),
+                   check_device=False)
+
+    for A in d64[:8]:
+        plain(A)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for A in d64:
+        plain(A)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    api.device_status()
+    del d64, flat, wsf
     return {"count": count, "ms_per_batch": ms, "matrices_per_s": count / (ms / 1e3),
             "alg_tflops": flops / (ms / 1e3) / 1e12, "alg_gflop_per_batch": flops / 1e9,
             "autotuned_variant": variant,
             "max_rel_err_vs_oracle_sample": max(errs), "sample_size": len(errs),
-            "fp64_plain_path_estimate_ms": est64_ms,
-            "fp64_estimate_method": "%d random matrices through cossin(fp64) one call each, %.2f s, scaled by flops share"
-                                    % (fp64_sample, t64),
-            "speedup_vs_fp64_plain_path": est64_ms / ms}
+            "sample": "2 largest orders, 3 largest norms, 6 random",
+            "fp64_plain_path_ms": 1e3 * t64,
+            "fp64_plain_path_method": "all %d matrices through cossin(fp64), one call each, wall clock" % count,
+            "speedup_vs_fp64_plain_path": 1e3 * t64 / ms}
 
 
 def ncu_case(name):
@@ -587,8 +613,9 @@ def ncu_case(name):
     import torch
     from paper_2010_00465_gb300 import api, inputs
     if name == "gemm_tf32":
-        A = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).float().cuda()
-        api.cossin(A, "fp32")
+        # the four-pass TF32 chain of the split form
+        A = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
+        api.cossin(A, "split_tf32")
     elif name == "batched":
         # 2,000 matrices of the batched workload's distribution, one launch
         ns, norms, fams = inputs.batch_shapes(2000, index=3)
@@ -622,8 +649,14 @@ def ncu_case(name):
     return 0
 
 
-def extra_launches(prec, info):
-    return 2  # splitting A and the final recombination
+def launches_of(prec, info):
+    """Kernels one cossin call launches: the 1-norm (2); FP64: one kernel per
+    product; FP32: the input conversion, per product the emulated product's
+    five slicing kernels, a memset and the product kernel, and the two output
+    conversions."""
+    if prec == "fp64":
+        return 2 + info["products"]
+    return 2 + 1 + 7 * info["products"] + 2
 
 
 def traffic_of(kernel):
@@ -656,6 +689,15 @@ def roofline(kind, ms, launches, work, pk, pk_kind, clocks):
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_of("gemm_f64_kernel"), "kernel": "gemm_f64_kernel",
                 "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x median SM clock under load (%.0f MHz)" % mhz}
+    if kind == "gemm_emu":
+        # the headline step's emulated products are the FP32 path's four-slice
+        # BF16 products: 10 slice products per algorithmic product
+        bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        issued = achieved * 10
+        return {"bound": "tensor", "achieved": issued, "peak": bf16, "unit": "TFLOP/s", "frac": issued / bf16,
+                "traffic": traffic_of("ozaki_kernel_s4"), "kernel": "ozaki_kernel<4>",
+                "peak_note": "%s sustained bf16 (the kernel runs inside a long step); achieved counts the 10 "
+                             "BF16 slice products of each product" % pk_kind, "algorithmic_tflops": achieved}
     # TF32 tensor: half the bf16 rate (nominal 1.1 vs 2.25 PFLOP/s); four passes per product
     bf16 = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     peak = bf16 * 1100.0 / 2250.0

@@ -44,23 +44,30 @@ typedef struct CUstream_st* cossin_stream_t;
 typedef enum {
   CS_OK = 0,
   CS_EINVAL = 1,      /* bad argument: size, alias, precision, forced (m, s), workspace */
-  CS_ENOMEM = 2,      /* a device allocation made by the library failed */
+  CS_ENOMEM = 2,      /* a device allocation made by the library failed (no work was queued) */
   CS_ENONFINITE = 3,  /* ||A||_1 is Inf or NaN */
   CS_ERANGE = 4,      /* the scaling would need s > 64 */
   CS_ECUDA = 5,       /* a CUDA runtime call failed (message has the CUDA error) */
-  CS_ETIMEOUT = 6     /* a device-side bounded wait expired (batched kernel) */
+  CS_ETIMEOUT = 6     /* a bounded wait in a tensor-core kernel expired in an earlier call */
 } cs_status;
 
 typedef enum {
   /* FP64 in and out; double table (u = 2^-53); every product in FP64. */
   CS_FP64 = 0,
-  /* FP32 in and out; single table (u = 2^-24); every product as a
-   * four-pass TF32 tensor-core product of (hi, lo) splits with FP32
-   * accumulation (promoted, compensated), linear combinations in FP32. */
+  /* FP32 in and out; single table (u = 2^-24).  The input is taken to FP64
+   * once; every product, the Taylor chain's and the double-angle steps', is
+   * a BF16 tensor-core product of four 7-bit slices per row / column (as
+   * CS_SPLIT_BF16's chain products) with FP64 intermediates, and C and S are
+   * rounded to FP32 once at the end (FP32-stored intermediates would let
+   * the double-angle recurrence amplify their rounding past 2e-5 at
+   * ||A||_1 near 64).  cossin_matmul with this prec forms the four-slice
+   * product of FP32 operands.  n <= 8192 (CS_EINVAL above). */
   CS_FP32 = 1,
   /* FP64 in and out; single table; the Taylor chain (steps 3-4) as
-   * four-pass TF32 tensor-core products, while the norm, the choice of
-   * (m, s) and the double-angle steps run in FP64.  Accuracy is FP32-level. */
+   * four-pass TF32 tensor-core products of (hi, lo) splits of FP64
+   * intermediates (the diagonal of the left operand added in FP64, the
+   * linear combinations in FP64), while the norm, the choice of (m, s) and
+   * the double-angle steps run in FP64. */
   CS_SPLIT_TF32 = 2,
   /* FP64 in and out; double table; every product emulated on the BF16
    * tensor cores: rows of the left and columns of the right operand cut into
@@ -84,6 +91,13 @@ typedef enum {
    * forms the four-slice product.  n <= 8192 (CS_EINVAL above). */
   CS_SPLIT_BF16 = 5
 } cs_prec;
+
+/* Status of the asynchronous part.  A call's status covers its arguments,
+ * its workspace and its 1-norm (read on the host before the products are
+ * queued); the products then run asynchronously, and a tensor-core product
+ * whose bounded wait expired (see cossin_device_status) is reported by the
+ * next call that reads the device error word, or by cossin_device_status
+ * after the stream is synchronised. */
 
 /* What one call did. */
 typedef struct {
@@ -192,13 +206,22 @@ cs_status cossin_cs(const void* A_dev, int64_t n, double t, cs_prec prec, void* 
  * once the kernel is queued on `stream`. */
 cs_status cossin_selftest_wait_timeout(cossin_stream_t stream);
 
+/* Allocation-failure self test (the paper has no counterpart): the next
+ * `count` device allocations the library makes for itself (the workspaces of
+ * cossin, cossin_cs, cossin_unitary without ws, cossin_norm1, cossin_matmul
+ * and the adjoint without ws) fail as if the device were out of memory, so
+ * those calls return CS_ENOMEM before queuing any work; later calls run
+ * normally.  count <= 0 clears the setting.  Host-only; touches no GPU. */
+void cossin_selftest_fail_next_alloc(int32_t count);
+
 /* One product P = X Y (n x n, row-major) on the library's product kernel for
  * `prec`, the one its Taylor chain uses: the FP64 kernel for CS_FP64, the
- * four-pass TF32 tensor-core kernel for CS_FP32 (FP32 in and out),
- * CS_SPLIT_TF32 and CS_SPLIT_EMU (FP64 in and out, computed from the FP32
- * roundings of X and Y), the eight-slice emulated product for CS_FP64_EMU
- * and the four-slice BF16 product for CS_SPLIT_BF16 (FP64 in and out,
- * n <= 8192 for these two).  These are the products the method counts (Pi_2m
+ * four-pass TF32 tensor-core kernel for CS_SPLIT_TF32 and CS_SPLIT_EMU (FP64
+ * in and out, computed from the (hi, lo) splits of X and Y), the eight-slice
+ * emulated product for CS_FP64_EMU and the four-slice BF16 product for
+ * CS_SPLIT_BF16 (FP64 in and out) and CS_FP32 (FP32 in and out, the
+ * operands taken to FP64 and the product rounded to FP32 once; n <= 8192
+ * for these three).  These are the products the method counts (Pi_2m
  * in Tables 1-2).  P must not overlap X or Y.  Allocates and frees a
  * stream-ordered workspace for the tensor-core kinds. */
 cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec prec, void* P_dev,
@@ -229,6 +252,25 @@ cs_status cossin_backward(int64_t count, int64_t n, const double* A_dev, const d
 cs_status cossin_backward_ex(int64_t count, int64_t n, const double* A_dev, const double* G_C_dev,
                              const double* G_S_dev, double* dA_dev, double* C_dev, double* S_dev, int32_t force_m,
                              int32_t force_s, cs_prec prec, cs_info* infos_host, cossin_stream_t stream);
+
+/* Caller-workspace forms of the adjoint (the `ws, ws_bytes` contract of
+ * cossin_ex): the same computation as cossin_backward_ex, with every device
+ * buffer taken from ws_dev and nothing allocated.  The buffers depend on the
+ * (2m, s) each matrix selects (its 1-norm, read on the device), so the size
+ * is queried for the largest s the caller expects:
+ *   cossin_backward_workspace_size: bytes for `count` matrices of order n in
+ *     `prec` (CS_FP64 or CS_FP64_EMU) whose selected or forced s are all
+ *     <= max_s, for any family.  Host-only.
+ *   cossin_backward_ws: ws_dev (256-byte aligned, not overlapping the
+ *     matrices) of ws_bytes; CS_EINVAL before any product is queued if the
+ *     pairs the norms select need more than ws_bytes (the message gives the
+ *     size).  Synchronises `stream` once for the norms and once per (2m, s)
+ *     group, as cossin_backward does. */
+cs_status cossin_backward_workspace_size(int64_t count, int64_t n, cs_prec prec, int32_t max_s, size_t* bytes);
+cs_status cossin_backward_ws(int64_t count, int64_t n, const double* A_dev, const double* G_C_dev,
+                             const double* G_S_dev, double* dA_dev, double* C_dev, double* S_dev, int32_t force_m,
+                             int32_t force_s, cs_prec prec, void* ws_dev, size_t ws_bytes, cs_info* infos_host,
+                             cossin_stream_t stream);
 
 /* ------------------------------------------------------------ unitary ---
  * The propagator U = e^{-itA} = cos(tA) - i sin(tA) of a real n x n matrix

@@ -65,6 +65,10 @@ SIGNATURES = {
     "cossin_batched_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "cossin_batched_plan_destroy": (ctypes.c_int, [_vp]),
     "cossin_selftest_wait_timeout": (ctypes.c_int, [_vp]),
+    "cossin_selftest_fail_next_alloc": (None, [_i32]),
+    "cossin_backward_workspace_size": (ctypes.c_int, [_i64, _i64, ctypes.c_int, _i32, ctypes.POINTER(_sz)]),
+    "cossin_backward_ws": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int, _vp, _sz,
+                                          _vp, _vp]),
     "cossin_last_error": (ctypes.c_char_p, []),
     "cossin_device_status": (ctypes.c_int, [_vp]),
     "cossin_prof_enable": (None, [_i32]),

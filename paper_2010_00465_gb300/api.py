@@ -65,6 +65,14 @@ def _check_matrix(A: torch.Tensor, p: int) -> int:
     return int(A.shape[0])
 
 
+def device_status(stream=None) -> None:
+    """Synchronise ``stream`` and raise CossinError(CS_ETIMEOUT) if a bounded
+    wait in a tensor-core kernel expired since the last check (the products
+    run asynchronously, so a call's own status covers only its arguments and
+    its 1-norm)."""
+    check(lib().cossin_device_status(_stream_ptr(stream)))
+
+
 def workspace_size(n: int, prec="fp64") -> int:
     out = ctypes.c_size_t()
     check(lib().cossin_workspace_size(int(n), _prec(prec), ctypes.byref(out)))
@@ -91,7 +99,8 @@ def select(norm: float, table: int):
 
 @_on_stream
 def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = None,
-           workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
+           workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False,
+           check_device: bool = True):
     """cos(A), sin(A) of a square matrix.
 
     ``prec``: "fp64", "fp32", "split_tf32", "fp64_emu", "split_emu" or
@@ -100,7 +109,11 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
     given as CPU tensors (pinned ones are filled by asynchronous copies on the
     call's stream, which is synchronised before returning), else into new CPU
     tensors.  For a device A, ``out`` holds device tensors.  ``m``/``s`` force
-    the family 2m and the number of double-angle steps.
+    the family 2m and the number of double-angle steps.  With
+    ``check_device`` (default) the call synchronises its stream at the end
+    and raises if a tensor-core kernel gave up on a bounded wait; without it
+    the call returns once the work is queued, and ``device_status`` reports
+    such a failure later.
     """
     p = _prec(prec, A)
     host = not A.is_cuda
@@ -132,6 +145,8 @@ def cossin(A: torch.Tensor, prec=None, *, m: int | None = None, s: int | None = 
                           ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
                           workspace.numel() * workspace.element_size(), fm, fs, ctypes.byref(info),
                           _stream_ptr(stream)))
+    if check_device:
+        device_status(stream)
     if host:
         if host_out is not None:
             host_out[0].copy_(C, non_blocking=host_out[0].is_pinned())
@@ -156,11 +171,13 @@ def cs_select(normB: float, table: int):
 
 @_on_stream
 def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None, sigma: int | None = None,
-              workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False):
+              workspace: torch.Tensor | None = None, out=None, stream=None, return_info: bool = False,
+              check_device: bool = True):
     """c(t^2 A) = cos(sqrt(t^2 A)) and s(t, A) = A^(-1/2) sin(sqrt(t^2 A)) (Sec. 2.2).
 
     ``family`` (0..3: 2, 3, 4 or 5 products) and ``sigma`` (double-angle
     steps) force the scheme; info["m"] is the family, info["norm1"] ||t^2 A||_1.
+    ``check_device`` as for ``cossin``.
     """
     p = _prec(prec, A)
     host = not A.is_cuda
@@ -183,6 +200,8 @@ def cossin_cs(A: torch.Tensor, t: float, prec=None, *, family: int | None = None
                           ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
                           workspace.numel() * workspace.element_size(), ff, fs, ctypes.byref(info),
                           _stream_ptr(stream)))
+    if check_device:
+        device_status(stream)
     if host:
         C = C.cpu()
         S = S.cpu()
@@ -201,16 +220,20 @@ def matmul(X: torch.Tensor, Y: torch.Tensor, prec=None, stream=None) -> torch.Te
     P = torch.empty_like(X)
     check(lib().cossin_matmul(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), n, p,
                               ctypes.c_void_p(P.data_ptr()), _stream_ptr(stream)))
+    device_status(stream)
     return P
 
 
 @_on_stream
 def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m: int | None = None,
                     s: int | None = None, want_forward: bool = False, stream=None, return_info: bool = False,
-                    prec: str = "fp64"):
+                    prec: str = "fp64", workspace: torch.Tensor | None = None):
     """Gradient of <G_C, cos(A)> + <G_S, sin(A)> (FP64; A is n x n or a
     [count, n, n] batch), at the (2m, s) the forward pass uses.  ``prec``
-    "fp64_emu" emulates the FP64 products on the BF16 tensor cores."""
+    "fp64_emu" emulates the FP64 products on the BF16 tensor cores.  With a
+    ``workspace`` (uint8 CUDA tensor of at least backward_workspace_size
+    bytes for the largest s the inputs select) the library allocates
+    nothing."""
     import numpy as np
     if A.dtype != torch.float64 or G_C.dtype != torch.float64 or G_S.dtype != torch.float64:
         raise TypeError("the adjoint runs in FP64")
@@ -233,11 +256,18 @@ def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m:
     infos = (CsInfo * max(count, 1))()
     fm = -1 if m is None else int(m)
     fs = -1 if s is None else int(s)
-    check(lib().cossin_backward_ex(count, n, ctypes.c_void_p(A3.data_ptr()), ctypes.c_void_p(GC3.data_ptr()),
-                                   ctypes.c_void_p(GS3.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
-                                   ctypes.c_void_p(C.data_ptr() if C is not None else 0),
-                                   ctypes.c_void_p(S.data_ptr() if S is not None else 0), fm, fs, _prec(prec),
-                                   infos, _stream_ptr(stream)))
+    ptrs = (count, n, ctypes.c_void_p(A3.data_ptr()), ctypes.c_void_p(GC3.data_ptr()),
+            ctypes.c_void_p(GS3.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
+            ctypes.c_void_p(C.data_ptr() if C is not None else 0),
+            ctypes.c_void_p(S.data_ptr() if S is not None else 0), fm, fs, _prec(prec))
+    if workspace is None:
+        check(lib().cossin_backward_ex(*ptrs, infos, _stream_ptr(stream)))
+    else:
+        if not workspace.is_cuda:
+            raise ValueError("the workspace must be a CUDA tensor")
+        check(lib().cossin_backward_ws(*ptrs, ctypes.c_void_p(workspace.data_ptr()),
+                                       workspace.numel() * workspace.element_size(), infos, _stream_ptr(stream)))
+    device_status(stream)
     if not batched:
         dA = dA[0]
         C = C[0] if C is not None else None
@@ -246,6 +276,19 @@ def cossin_backward(A: torch.Tensor, G_C: torch.Tensor, G_S: torch.Tensor, *, m:
     if return_info:
         return out, [infos[i].as_dict() for i in range(count)]
     return out
+
+
+def backward_workspace_size(count: int, n: int, max_s: int, prec: str = "fp64") -> int:
+    """Bytes of the caller workspace of cossin_backward for ``count`` matrices
+    of order n whose (2m, s) have s <= max_s."""
+    out = ctypes.c_size_t()
+    check(lib().cossin_backward_workspace_size(int(count), int(n), _prec(prec), int(max_s), ctypes.byref(out)))
+    return int(out.value)
+
+
+def selftest_fail_next_alloc(count: int = 1) -> None:
+    """Test hook: the library's next ``count`` device allocations fail (CS_ENOMEM)."""
+    lib().cossin_selftest_fail_next_alloc(int(count))
 
 
 def unitary_workspace_size(n: int, prec="fp64") -> int:
@@ -272,6 +315,7 @@ def unitary(A: torch.Tensor, t: float, prec=None, *, m: int | None = None, s: in
     check(lib().cossin_unitary(ctypes.c_void_p(A.data_ptr()), n, float(t), p, ctypes.c_void_p(U.data_ptr()),
                                ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
                                fm, fs, ctypes.byref(info), _stream_ptr(stream)))
+    device_status(stream)
     return (U, info.as_dict()) if return_info else U
 
 

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -168,6 +169,36 @@ Ssa make_ssa(int m, int s, double scale) {
   return g;
 }
 
+// Device memory of one backward call: bump allocation from the caller's
+// workspace (mark / release per (2m, s) group), or stream-ordered
+// allocations of the library's own when no workspace is given.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  cudaStream_t st = nullptr;
+  std::vector<void*> owned;
+  cs_status get(void** p, size_t bytes, const char* what) {
+    if (!base) {
+      CS_CHECK(dev_alloc(p, bytes, st, what));
+      owned.push_back(*p);
+      return CS_OK;
+    }
+    const size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > cap) return fail(CS_EINVAL, std::string("backward workspace too small at ") + what);
+    *p = base + off;
+    used = off + bytes;
+    return CS_OK;
+  }
+  // frees (or returns to the bump pointer) everything taken after `mark`
+  void release(size_t mark, size_t nowned) {
+    while (owned.size() > nowned) {
+      cudaFreeAsync(owned.back(), st);
+      owned.pop_back();
+    }
+    used = mark;
+  }
+};
+
 // Accumulating product: Acc += op(X) op(Y), batched with stride n^2.
 cs_status gemm_acc(const AdjProd& prod, const double* X, bool tX, const double* Y, bool tY, double* Acc,
                    double scale, int64_t n, int64_t batch, cudaStream_t stream) {
@@ -181,8 +212,13 @@ cs_status gemm_acc(const AdjProd& prod, const double* X, bool tX, const double* 
   return prod(X, tX, Y, tY, e, n, batch, stream);
 }
 
+// Values one group's forward tape keeps per matrix (chain values and the
+// double-angle levels), which sizes its buffer.
+int tape_values(int m, int s) { return make_ssa(m, s, 1.0).nvalues + 2 * s; }
+
 cs_status run_group(const double* A, const double* GC, const double* GS, double* dA, double* C_out, double* S_out,
-                    int64_t n, int m, int s, int64_t g, double scale, const AdjProd& prod, cudaStream_t stream) {
+                    int64_t n, int m, int s, int64_t g, double scale, const AdjProd& prod, Arena& arena,
+                    cudaStream_t stream) {
   const Ssa ssa = make_ssa(m, s, scale);
   const int64_t n2 = n * n;
   const int nlev = s + 1;
@@ -194,7 +230,8 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
   const size_t per = sizeof(double) * (size_t)n2 * (size_t)g;
   const size_t total = per * (size_t)(2 * nval + 1);
   char* buf = nullptr;
-  CS_CUDA_CHECK(cudaMallocAsync((void**)&buf, total, stream));
+  const size_t mark = arena.used, nowned = arena.owned.size();
+  CS_CHECK(arena.get((void**)&buf, total, "the adjoint's tape"));
   auto val = [&](int v) { return (double*)(buf + per * (size_t)v); };
   auto adj = [&](int v) { return (double*)(buf + per * (size_t)(nval + v)); };
   double* phat = (double*)(buf + per * (size_t)(2 * nval));
@@ -269,7 +306,7 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
   }
   if (rc == CS_OK) ce = cudaMemcpyAsync(dA, adj(ssa.A), per, cudaMemcpyDeviceToDevice, stream);
   if (rc == CS_OK && ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync");
-  cudaFreeAsync(buf, stream);
+  arena.release(mark, nowned);
   return rc;
 }
 
@@ -277,11 +314,33 @@ cs_status run_group(const double* A, const double* GC, const double* GS, double*
 
 int64_t adjoint_products(int m, int s) { return 3 * products_of(m) + 6 * s; }
 
+namespace {
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device bytes of one (2m, s) group of g matrices of order n: gathered
+// inputs and outputs (6 n^2 g doubles and the index list), the emulated
+// products' scratch and transposes, and the tape.
+size_t group_bytes(int64_t n, int64_t g, int m, int s, bool emu) {
+  const size_t per = sizeof(double) * (size_t)n * (size_t)n * (size_t)g;
+  size_t b = al256(6 * per + sizeof(int) * (size_t)g);
+  if (emu) b += al256(ozaki_dims(n, n, n, g).total + 2 * per);
+  b += al256(per * (size_t)(2 * tape_values(m, s) + 1));
+  return b;
+}
+}  // namespace
+
+size_t backward_workspace_bytes(int64_t count, int64_t n, int max_s, bool emu) {
+  int worst_m = 4;
+  for (int m : {4, 8, 9, 16, 24})
+    if (tape_values(m, max_s) > tape_values(worst_m, max_s)) worst_m = m;
+  return al256(sizeof(double) * (size_t)count) + group_bytes(n, count, worst_m, max_s, emu);
+}
+
 // Gradient of <G_C, r_c(scale A)> + <G_S, r_s(scale A)> with respect to A; the
 // scale sits in the plans' coefficients, so the reverse pass carries it.
 cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A, const double* G_C,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
-                        cs_info* infos_host, cudaStream_t st, bool emu) {
+                        cs_info* infos_host, cudaStream_t st, bool emu, void* ws, size_t ws_bytes) {
   if (count < 0 || n < 0 || n > kMaxN) return fail(CS_EINVAL, "count or n out of range");
   if (n > 0 && count > (int64_t(1) << 46) / (n * n)) return fail(CS_EINVAL, "count * n^2 above 2^46 elements");
   if (emu && n > kOzakiMaxK) return fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
@@ -298,20 +357,34 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
   };
   if (ov(dA, A) || ov(dA, G_C) || ov(dA, G_S) || ov(C, A) || ov(S, A) || ov(C, S) || ov(C, dA) || ov(S, dA))
     return fail(CS_EINVAL, "outputs must not overlap inputs or each other");
+  Arena arena;
+  arena.st = st;
+  if (ws) {
+    if (((uintptr_t)ws & 255) != 0) return fail(CS_EINVAL, "workspace must be 256-byte aligned");
+    const size_t allw = (size_t)n * (size_t)n * (size_t)count * sizeof(double);
+    if (overlaps(ws, ws_bytes, A, allw) || overlaps(ws, ws_bytes, G_C, allw) || overlaps(ws, ws_bytes, G_S, allw) ||
+        overlaps(ws, ws_bytes, dA, allw) || (C && overlaps(ws, ws_bytes, C, allw)) ||
+        (S && overlaps(ws, ws_bytes, S, allw)))
+      return fail(CS_EINVAL, "workspace must not overlap the matrices");
+    arena.base = (char*)ws;
+    arena.cap = ws_bytes;
+  }
   // norms of every matrix, one synchronisation
   std::vector<double> norms((size_t)count);
   {
     double* outs = nullptr;
-    CS_CUDA_CHECK(cudaMallocAsync((void**)&outs, sizeof(double) * count, st));
+    CS_CHECK(arena.get((void**)&outs, sizeof(double) * count, "the norms"));
     cs_status rc = norm1_batched_f64(A, n, count, outs, st);
     cudaError_t ce = rc == CS_OK ? cudaMemcpyAsync(norms.data(), outs, sizeof(double) * count, cudaMemcpyDeviceToHost, st)
                                  : cudaSuccess;
     cudaError_t ce2 = cudaStreamSynchronize(st);
-    cudaFreeAsync(outs, st);
+    arena.release(0, 0);
     if (rc != CS_OK) return rc;
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpyAsync");
     if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");
   }
+  // with the norms out of the way the groups take the whole workspace
+  arena.used = 0;
   for (double& v : norms) v *= fabs(scale);
   std::map<std::pair<int, int>, std::vector<int>> groups;
   for (int64_t b = 0; b < count; ++b) {
@@ -329,6 +402,14 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
       infos_host[b] = cs_info{norms[b], m, s, prods, 0, 2.0 * (double)n * n * n * prods};
     }
   }
+  if (ws) {
+    size_t need = 0;
+    for (auto& kv : groups)
+      need = std::max(need, group_bytes(n, (int64_t)kv.second.size(), kv.first.first, kv.first.second, emu));
+    if (need > ws_bytes)
+      return fail(CS_EINVAL, "backward workspace too small: the selected (2m, s) need " + std::to_string(need) +
+                                 " bytes (cossin_backward_workspace_size with the largest s)");
+  }
   for (auto& kv : groups) {
     const int m = kv.first.first, s = kv.first.second;
     const std::vector<int>& idx = kv.second;
@@ -336,7 +417,8 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
     const size_t per = sizeof(double) * (size_t)n2 * (size_t)g;
     const bool need_c = C != nullptr, need_s = S != nullptr;
     char* gb = nullptr;
-    CS_CUDA_CHECK(cudaMallocAsync((void**)&gb, 6 * per + sizeof(int) * g, st));
+    const size_t mark = arena.used, nowned = arena.owned.size();
+    CS_CHECK(arena.get((void**)&gb, 6 * per + sizeof(int) * g, "the gathered matrices"));
     double* gA = (double*)gb;
     double* gGC = (double*)(gb + per);
     double* gGS = (double*)(gb + 2 * per);
@@ -362,17 +444,17 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
       prod.err = tc_error_word();
       prod.work_bytes = ozaki_dims(n, n, n, g).total;
       const size_t tb = sizeof(double) * (size_t)n2 * (size_t)g;
-      ce = cudaMallocAsync((void**)&eb, prod.work_bytes + 2 * tb, st);
-      if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaMallocAsync");
-      if (!prod.err) rc = fail(CS_ECUDA, "cannot resolve the device error word");
+      rc = arena.get((void**)&eb, prod.work_bytes + 2 * tb, "the emulated products' scratch");
+      if (rc == CS_OK && !prod.err) rc = fail(CS_ECUDA, "cannot resolve the device error word");
       if (rc == CS_OK) {
         prod.work = eb;
         prod.tbuf[0] = (double*)(eb + prod.work_bytes);
         prod.tbuf[1] = (double*)(eb + prod.work_bytes + tb);
       }
     }
-    if (rc == CS_OK) rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, scale, prod, st);
-    if (eb) cudaFreeAsync(eb, st);
+    if (rc == CS_OK)
+      rc = run_group(gA, gGC, gGS, gdA, need_c ? gC : nullptr, need_s ? gS : nullptr, n, m, s, g, scale, prod, arena,
+                     st);
     if (rc == CS_OK) {
       scatter_kernel<<<nb, 256, 0, st>>>(gdA, dA, didx, n2, g);
       if (need_c) scatter_kernel<<<nb, 256, 0, st>>>(gC, C, didx, n2, g);
@@ -382,7 +464,7 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
     }
     // the host index vector must outlive its copy
     cudaError_t ce2 = cudaStreamSynchronize(st);
-    cudaFreeAsync(gb, st);
+    arena.release(mark, nowned);
     if (rc != CS_OK) return rc;
     if (ce2 != cudaSuccess) return cuda_fail(ce2, "cudaStreamSynchronize");
   }
@@ -395,7 +477,7 @@ extern "C" cs_status cossin_backward(int64_t count, int64_t n, const double* A, 
                                      const double* G_S, double* dA, double* C, double* S, int32_t force_m,
                                      int32_t force_s, cs_info* infos_host, cossin_stream_t stream) {
   return cs::backward_impl(count, n, 1.0, A, G_C, G_S, dA, C, S, force_m, force_s, infos_host,
-                           (cudaStream_t)stream, false);
+                           (cudaStream_t)stream, false, nullptr, 0);
 }
 
 extern "C" cs_status cossin_backward_ex(int64_t count, int64_t n, const double* A, const double* G_C,
@@ -403,5 +485,27 @@ extern "C" cs_status cossin_backward_ex(int64_t count, int64_t n, const double* 
                                         int32_t force_s, cs_prec prec, cs_info* infos_host, cossin_stream_t stream) {
   if (prec != CS_FP64 && prec != CS_FP64_EMU) return cs::fail(CS_EINVAL, "the adjoint runs in CS_FP64 or CS_FP64_EMU");
   return cs::backward_impl(count, n, 1.0, A, G_C, G_S, dA, C, S, force_m, force_s, infos_host,
-                           (cudaStream_t)stream, prec == CS_FP64_EMU);
+                           (cudaStream_t)stream, prec == CS_FP64_EMU, nullptr, 0);
+}
+
+extern "C" cs_status cossin_backward_workspace_size(int64_t count, int64_t n, cs_prec prec, int32_t max_s,
+                                                    size_t* bytes) {
+  if (!bytes) return cs::fail(CS_EINVAL, "bytes is null");
+  if (prec != CS_FP64 && prec != CS_FP64_EMU) return cs::fail(CS_EINVAL, "the adjoint runs in CS_FP64 or CS_FP64_EMU");
+  if (count < 0 || n < 0 || n > cs::kMaxN) return cs::fail(CS_EINVAL, "count or n out of range");
+  if (n > 0 && count > (int64_t(1) << 46) / (n * n)) return cs::fail(CS_EINVAL, "count * n^2 above 2^46 elements");
+  if (prec == CS_FP64_EMU && n > cs::kOzakiMaxK) return cs::fail(CS_EINVAL, "the emulated FP64 products support n <= 8192");
+  if (max_s < 0 || max_s > cs::kMaxS) return cs::fail(CS_EINVAL, "max_s must be in [0, 64]");
+  *bytes = (count == 0 || n == 0) ? 0 : cs::backward_workspace_bytes(count, n, max_s, prec == CS_FP64_EMU);
+  return CS_OK;
+}
+
+extern "C" cs_status cossin_backward_ws(int64_t count, int64_t n, const double* A, const double* G_C,
+                                        const double* G_S, double* dA, double* C, double* S, int32_t force_m,
+                                        int32_t force_s, cs_prec prec, void* ws, size_t ws_bytes, cs_info* infos_host,
+                                        cossin_stream_t stream) {
+  if (prec != CS_FP64 && prec != CS_FP64_EMU) return cs::fail(CS_EINVAL, "the adjoint runs in CS_FP64 or CS_FP64_EMU");
+  if (!ws && count > 0 && n > 0) return cs::fail(CS_EINVAL, "workspace is null");
+  return cs::backward_impl(count, n, 1.0, A, G_C, G_S, dA, C, S, force_m, force_s, infos_host,
+                           (cudaStream_t)stream, prec == CS_FP64_EMU, ws, ws_bytes);
 }

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -30,6 +31,25 @@ cs_status fail(cs_status st, const std::string& msg) {
 cs_status cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
   return CS_ECUDA;
+}
+
+// ------------------------------------------------------------ allocation ---
+static std::atomic<int> g_fail_allocs{0};
+
+cs_status dev_alloc(void** p, size_t bytes, cudaStream_t stream, const char* what) {
+  *p = nullptr;
+  int left = g_fail_allocs.load();
+  while (left > 0 && !g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left > 0) return fail(CS_ENOMEM, std::string(what) + ": allocation failed (injected)");
+  const cudaError_t e = cudaMallocAsync(p, bytes, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(CS_ENOMEM, std::string(what) + ": allocation of " + std::to_string(bytes) +
+                               " bytes failed: " + cudaGetErrorString(e));
+  }
+  return CS_OK;
 }
 
 // ------------------------------------------------------------- profiling ---
@@ -613,7 +633,7 @@ cs_status cossin_norm1(const void* A, int64_t n, cs_prec prec, double* norm1, co
   const size_t part = sizeof(double) * ((size_t)cs::norm1_scratch_elems(n) + 1);
   void* buf = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
-  CS_CUDA_CHECK(cudaMallocAsync(&buf, part, st));
+  CS_CHECK(cs::dev_alloc(&buf, part, st, "cossin_norm1 scratch"));
   double* out = (double*)buf;
   double* partial = out + 1;
   cs_status rc = prec == CS_FP32 ? cs::norm1_f32((const float*)A, n, partial, out, st)
@@ -645,11 +665,7 @@ cs_status cossin(const void* A, int64_t n, cs_prec prec, void* C, void* S, cossi
   size_t bytes = cs::make_layout(n, prec).total;
   void* ws = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMallocAsync(&ws, bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cs::fail(CS_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
-  }
+  CS_CHECK(cs::dev_alloc(&ws, bytes, st, "cossin workspace"));
   cs_status rc = cs::cossin_impl(A, n, prec, C, S, ws, bytes, -1, -1, nullptr, st, 1.0);
   cudaFreeAsync(ws, st);
   return rc;
@@ -684,7 +700,7 @@ cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, v
   if (!prod.err) return cs::fail(CS_ECUDA, "cannot resolve the device error word");
   const size_t conv = f32 ? (3 * sizeof(double) * n2 + 255) & ~(size_t)255 : 0;
   char* buf = nullptr;
-  CS_CUDA_CHECK(cudaMallocAsync((void**)&buf, conv + prod.emu_bytes, st));
+  CS_CHECK(cs::dev_alloc((void**)&buf, conv + prod.emu_bytes, st, "cossin_matmul scratch"));
   prod.emu_work = buf + conv;
   const double* X64 = (const double*)X;
   const double* Y64 = (const double*)Y;
@@ -712,11 +728,7 @@ cs_status cossin_cs(const void* A, int64_t n, double t, cs_prec prec, void* C, v
   if (n == 0) return cs::cs_impl(A, n, t, prec, C, S, nullptr, 0, force_family, force_sigma, info, st);
   const size_t bytes = cs::make_layout(n, prec).total;
   void* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cs::fail(CS_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
-  }
+  CS_CHECK(cs::dev_alloc(&buf, bytes, st, "cossin_cs workspace"));
   cs_status rc = cs::cs_impl(A, n, t, prec, C, S, buf, bytes, force_family, force_sigma, info, st);
   cudaFreeAsync(buf, st);
   return rc;
@@ -734,6 +746,8 @@ cs_status cossin_cs_select(double normB, int32_t table, int32_t* family, int32_t
   *sigma = sg;
   return CS_OK;
 }
+
+void cossin_selftest_fail_next_alloc(int32_t count) { cs::g_fail_allocs.store(count > 0 ? count : 0); }
 
 cs_status cossin_selftest_wait_timeout(cossin_stream_t stream) {
   // about 1 ms at 2 GHz: the kernel gives up, raises the error word, returns

@@ -22,6 +22,10 @@ cs_status cuda_fail(cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return ::cs::cuda_fail(e_, #expr); \
   } while (0)
 
+// Stream-ordered device allocation of the library's own buffers; a failure
+// (or one injected by cossin_selftest_fail_next_alloc) returns CS_ENOMEM.
+cs_status dev_alloc(void** p, size_t bytes, cudaStream_t stream, const char* what);
+
 #define CS_CHECK(expr)                       \
   do {                                       \
     cs_status st_ = (expr);                  \
@@ -135,9 +139,14 @@ cs_status convert_f64_f32(const double* src, float* dst, int64_t count, cudaStre
 // adjoint of scale * A.
 cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, void* ws, size_t ws_bytes,
                       int32_t force_m, int32_t force_s, cs_info* info, cudaStream_t stream, double scale);
+// backward_impl: with ws null the library allocates its buffers
+// stream-ordered; else it takes them from ws (ws_bytes, 256-byte aligned) and
+// allocates nothing.
 cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A, const double* G_C,
                         const double* G_S, double* dA, double* C, double* S, int32_t force_m, int32_t force_s,
-                        cs_info* infos_host, cudaStream_t stream, bool emu = false);
+                        cs_info* infos_host, cudaStream_t stream, bool emu = false, void* ws = nullptr,
+                        size_t ws_bytes = 0);
+size_t backward_workspace_bytes(int64_t count, int64_t n, int max_s, bool emu);
 cs_status check_prec(cs_prec prec);
 // Every precision keeps FP64 intermediates.  uses_emu: some products are
 // sliced BF16 tensor-core products (CS_FP64_EMU, CS_SPLIT_EMU, CS_SPLIT_BF16,

@@ -217,7 +217,7 @@ cs_status matmul_tf32(const void* X, const void* Y, int64_t n, bool f64_io, void
   const int64_t ld = (n + 31) / 32 * 32;
   const size_t sz = sizeof(float) * (size_t)n * (size_t)ld;
   char* ws = nullptr;
-  CS_CUDA_CHECK(cudaMallocAsync((void**)&ws, 8 * sz, stream));
+  CS_CHECK(dev_alloc((void**)&ws, 8 * sz, stream, "cossin_matmul scratch"));
   float* b[8];
   for (int k = 0; k < 8; ++k) b[k] = (float*)(ws + k * sz);
   cs_status rc;

@@ -73,11 +73,7 @@ extern "C" cs_status cossin_unitary(const void* A, int64_t n, double t, cs_prec 
   const Layout L = make_layout(n, prec, true);
   void* buf = nullptr;
   if (!ws) {
-    cudaError_t e = cudaMallocAsync(&buf, L.total, st);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(CS_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
-    }
+    CS_CHECK(dev_alloc(&buf, L.total, st, "cossin_unitary workspace"));
     ws = buf;
     ws_bytes = L.total;
   }
@@ -121,7 +117,7 @@ extern "C" cs_status cossin_unitary_backward(int64_t count, int64_t n, double t,
     return fail(CS_EINVAL, "outputs must not overlap inputs or each other");
   char* buf = nullptr;
   const size_t need = (U ? 4 : 2) * real_bytes;
-  CS_CUDA_CHECK(cudaMallocAsync((void**)&buf, need, st));
+  CS_CHECK(dev_alloc((void**)&buf, need, st, "cossin_unitary_backward scratch"));
   double* GC = (double*)buf;
   double* GS = (double*)(buf + real_bytes);
   double* C = U ? (double*)(buf + 2 * real_bytes) : nullptr;

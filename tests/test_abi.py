@@ -208,3 +208,45 @@ def test_precision_selects_its_table(L, prec, table):
     info = _lib.CsInfo()
     assert L.cossin_cs(nul, 0, 1.0, prec, nul, nul, nul, 0, -1, -1, ctypes.byref(info), nul) == _lib.CS_OK
     assert info.table == table
+
+
+def test_backward_workspace_size_host_only(L):
+    small = api.backward_workspace_size(4, 64, 0)
+    assert small > 4 * 64 * 64 * 8 * 6
+    assert api.backward_workspace_size(4, 64, 3) > small          # deeper tape with more double-angle levels
+    assert api.backward_workspace_size(8, 64, 3) > api.backward_workspace_size(4, 64, 3)
+    assert api.backward_workspace_size(4, 64, 3, "fp64_emu") > api.backward_workspace_size(4, 64, 3)
+    assert api.backward_workspace_size(0, 64, 3) == 0
+    for bad in (dict(max_s=-1), dict(max_s=65), dict(prec="fp32")):
+        kw = dict(count=4, n=64, max_s=3)
+        kw.update(bad)
+        with pytest.raises(_lib.CossinError) as e:
+            api.backward_workspace_size(**kw)
+        assert e.value.status == _lib.CS_EINVAL
+
+
+def test_backward_ws_rejects_missing_workspace(L):
+    fake = ctypes.c_void_p(1 << 20)
+    st = L.cossin_backward_ws(2, 8, fake, fake, fake, fake, None, None, -1, -1, _lib.CS_FP64, None, 0, None, None)
+    assert st == _lib.CS_EINVAL and b"workspace" in L.cossin_last_error()
+
+
+def test_injected_allocation_failure_returns_enomem(L):
+    """The allocation-failure knob: each entry point that allocates returns
+    CS_ENOMEM before queuing any work (no GPU is touched here), and the knob
+    is used up by exactly the requested number of allocations."""
+    a = ctypes.c_void_p(1 << 20)
+    c = ctypes.c_void_p(2 << 20)
+    s = ctypes.c_void_p(3 << 20)
+    api.selftest_fail_next_alloc(4)
+    assert L.cossin(a, 64, _lib.CS_FP64, c, s, None) == _lib.CS_ENOMEM
+    assert b"cossin workspace" in L.cossin_last_error()
+    nrm = ctypes.c_double()
+    assert L.cossin_norm1(a, 64, _lib.CS_FP64, ctypes.byref(nrm), None) == _lib.CS_ENOMEM
+    assert L.cossin_cs(a, 64, 0.5, _lib.CS_FP64, c, s, None, 0, -1, -1, None, None) == _lib.CS_ENOMEM
+    u = ctypes.c_void_p(8 << 20)
+    assert L.cossin_unitary(a, 64, 0.5, _lib.CS_FP64, u, None, 0, -1, -1, None, None) == _lib.CS_ENOMEM
+    api.selftest_fail_next_alloc(1)
+    da = ctypes.c_void_p(16 << 20)
+    assert L.cossin_backward(2, 64, a, c, s, da, None, None, -1, -1, None, None) == _lib.CS_ENOMEM
+    api.selftest_fail_next_alloc(0)

@@ -171,3 +171,24 @@ def test_emulated_adjoint_argument_errors():
     with pytest.raises(_lib.CossinError) as ex:
         api.cossin_backward(A, A, A, prec="fp32")
     assert ex.value.status == _lib.CS_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_emu"])
+def test_caller_workspace_form_matches(prec):
+    """cossin_backward_ws takes every buffer from the caller's workspace and
+    gives the same gradient and forward outputs as the allocating form;
+    a workspace below what the selected pairs need is refused before any work."""
+    A, GC, GS = inputs.hamiltonian_batch(24, 48, index=9)
+    Ad, GCd, GSd = cuda(A), cuda(GC), cuda(GS)
+    (dA0, C0, S0), infos = api.cossin_backward(Ad, GCd, GSd, want_forward=True, return_info=True, prec=prec)
+    max_s = max(i["s"] for i in infos)
+    need = api.backward_workspace_size(24, 48, max_s, prec)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    dA1, C1, S1 = api.cossin_backward(Ad, GCd, GSd, want_forward=True, prec=prec, workspace=ws)
+    assert torch.equal(dA0, dA1) and torch.equal(C0, C1) and torch.equal(S0, S1)
+    ref = oracle.gradient(A[3], GC[3], GS[3], infos[3]["m"], infos[3]["s"])
+    assert np.linalg.norm(dA1[3].cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-11
+    small = torch.empty(need // 4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(_lib.CossinError) as ex:
+        api.cossin_backward(Ad, GCd, GSd, prec=prec, workspace=small)
+    assert ex.value.status == _lib.CS_EINVAL

@@ -32,3 +32,34 @@ def test_expired_wait_is_reported_once_and_the_context_stays_usable():
         Co, So, _ = oracle.cossin(x.double().cpu().numpy(), "single" if prec == "fp32" else "double")
         assert float(np.linalg.norm(C.double().cpu().numpy() - Co) / np.linalg.norm(Co)) <= tol
         assert float(np.linalg.norm(S.double().cpu().numpy() - So) / np.linalg.norm(So)) <= tol
+
+
+def test_injected_allocation_failure_then_normal_calls():
+    """A failed workspace allocation (injected on the host) returns CS_ENOMEM
+    with no work queued; the next calls allocate and compute normally."""
+    A = inputs.matrix(40, "normal", 3.0, index=211)
+    Ad = torch.from_numpy(A).cuda()
+    Co, So, _ = oracle.cossin(A)
+    api.selftest_fail_next_alloc(1)
+    with pytest.raises(_lib.CossinError) as ex:
+        api.norm1(Ad)
+    assert ex.value.status == _lib.CS_ENOMEM
+    assert api.norm1(Ad) == pytest.approx(oracle.norm1(A), rel=1e-14)
+    C = torch.empty_like(Ad)
+    S = torch.empty_like(Ad)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    call = lambda: _lib.lib().cossin(ctypes.c_void_p(Ad.data_ptr()), 40, _lib.CS_FP64, ctypes.c_void_p(C.data_ptr()),
+                                     ctypes.c_void_p(S.data_ptr()), stream)
+    api.selftest_fail_next_alloc(1)
+    assert call() == _lib.CS_ENOMEM
+    assert call() == _lib.CS_OK
+    api.device_status()
+    assert float(np.linalg.norm(C.cpu().numpy() - Co) / np.linalg.norm(Co)) <= 1e-11
+    assert float(np.linalg.norm(S.cpu().numpy() - So) / np.linalg.norm(So)) <= 1e-11
+    G = torch.from_numpy(inputs.matrix(40, "normal", None, index=212)).cuda()
+    api.selftest_fail_next_alloc(1)
+    with pytest.raises(_lib.CossinError) as ex:
+        api.cossin_backward(Ad, G, G)
+    assert ex.value.status == _lib.CS_ENOMEM
+    dA = api.cossin_backward(Ad, G, G)
+    assert torch.isfinite(dA).all()
