@@ -252,6 +252,10 @@ def main():
     flops_per_step = sum(i["flops"] for i in infos)
     launches_per_step = sum(launches_of(p, i) for (p, _, _), i in zip(work, infos))
 
+    # the FP64 roofline's denominator, measured on this GPU (register-only FMAs)
+    fp64_probe = max(api.fp64_fma_rate() for _ in range(3))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
     api.prof_reset()
     api.prof_enable(True)
     with ClockSampler(local) as clk:
@@ -334,6 +338,8 @@ def main():
     dominant = max(("gemm_f64", "gemm_emu"), key=lambda k: kern[k][0])
     clocks = clk.summary()
     pk, pk_kind = peaks()
+    pk["fp64_probe_tflops"] = fp64_probe
+    pk["sm_count"] = sm_count
     roof = roofline(dominant, *kern[dominant], pk, pk_kind, clocks)
     other = "gemm_emu" if dominant == "gemm_f64" else "gemm_f64"
     roof_other = roofline(other, *kern[other], pk, pk_kind, clocks)
@@ -367,6 +373,13 @@ def main():
                      for (p, f, r), i, t in zip(work, infos, case_ms)],
         "kernels": {k: {"ms": v[0], "launches": v[1], "work": v[2]} for k, v in kern.items()},
     }
+    if ws > 1 and not args.no_forms:
+        # every matrix of a batch is independent: the batched workload and
+        # the adjoint's control workload split over the ranks (no collective
+        # while computing; results gathered to rank 0 afterwards)
+        sh = sharded_forms()
+        if rank == 0:
+            line["sharded"] = sh
     if rank == 0 and not args.no_forms:
         line["forms"] = forms(api, wsp)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -378,6 +391,27 @@ def main():
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def sharded_forms(count=20000, adj_count=512, adj_n=128):
+    """With N ranks: the 20,000-matrix batched workload and the 512-matrix
+    adjoint workload, each split over the ranks by sharding.shard (LPT on
+    n^3), each rank's share one batched launch; the time is the slowest
+    rank's, the rate the whole batch over it (strong scaling: the batch is
+    fixed as N grows)."""
+    from paper_2010_00465_gb300 import inputs, sharded
+    ns, norms, fams = inputs.batch_shapes(count, index=3)
+    make = lambda i: inputs.matrix(int(ns[i]), str(fams[i]), float(norms[i]), index=3, sub=i + 1).astype(np.float32)
+    b = sharded.run_sharded(ns, make, sharded.batched_compute())
+    A, GC, GS = inputs.hamiltonian_batch(adj_count, adj_n)
+    a = sharded.run_sharded(np.full(adj_count, adj_n), lambda i: (A[i], GC[i], GS[i]), sharded.adjoint_compute())
+    out = {"scaling": "strong", "partition": "greedy LPT on n^3 (sharding.shard)"}
+    if "seconds_max" in b:
+        out["batched"] = {"count": count, "ms_slowest_rank": 1e3 * b["seconds_max"],
+                          "matrices_per_s": count / b["seconds_max"]}
+        out["adjoint"] = {"count": adj_count, "n": adj_n, "ms_slowest_rank": 1e3 * a["seconds_max"],
+                          "matrices_per_s": adj_count / a["seconds_max"]}
+    return out
 
 
 def forms(api, wsp):
@@ -683,12 +717,17 @@ def roofline(kind, ms, launches, work, pk, pk_kind, clocks):
     per_launch_s = ms / 1e3 / launches
     achieved = work / launches / per_launch_s / 1e12
     if kind == "gemm_f64":
-        # FP64 FMA units: 2 per SM per clock (1.25 TFLOP/s at 2070 MHz over 152 SMs)
+        # FP64 FMA units: measured by the register-only probe in this run;
+        # the nominal 2 FMA/clk/SM x SMs x clock beside it
         mhz = clocks.get("sm_mhz") or 2070.0
-        peak = 2 * 2 * 152 * mhz * 1e6 / 1e12
+        sms = pk.get("sm_count", 152)
+        nominal = 2 * 2 * sms * mhz * 1e6 / 1e12
+        peak = pk.get("fp64_probe_tflops") or nominal
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_of("gemm_f64_kernel"), "kernel": "gemm_f64_kernel",
-                "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x median SM clock under load (%.0f MHz)" % mhz}
+                "peak_note": "measured: cossin_fp64_fma_rate (16 independent FP64 FMA chains per thread, %d SMs x 4 "
+                             "CTAs x 256 threads, best of 3) in this run, %.4f TFLOP/s; nominal 2 FMA/clk/SM x %d "
+                             "SMs x median SM clock under load (%.0f MHz) = %.4f" % (sms, peak, sms, mhz, nominal)}
     if kind == "gemm_emu":
         # the headline step's emulated products are the FP32 path's four-slice
         # BF16 products: 10 slice products per algorithmic product
@@ -726,6 +765,27 @@ def accuracy(api, dev_in, outs, work):
         torch.cuda.synchronize()
         ts.append(time.perf_counter() - t0)
     res["fp64_64x64_latency_us"] = float(np.median(ts) * 1e6)
+    # the same call at the C ABI with caller-provided workspace and outputs
+    # (no Python-side allocation), median of 200
+    import ctypes
+    from paper_2010_00465_gb300 import _lib
+    L = _lib.lib()
+    wsn = torch.empty(api.workspace_size(64, "fp64"), dtype=torch.uint8, device="cuda")
+    Cn, Sn = torch.empty_like(Ad), torch.empty_like(Ad)
+    info = _lib.CsInfo()
+    cargs = (ctypes.c_void_p(Ad.data_ptr()), 64, _lib.CS_FP64, ctypes.c_void_p(Cn.data_ptr()),
+             ctypes.c_void_p(Sn.data_ptr()), ctypes.c_void_p(wsn.data_ptr()), wsn.numel(), -1, -1,
+             ctypes.byref(info), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    ts = []
+    for _ in range(200):
+        t0 = time.perf_counter()
+        _lib.check(L.cossin_ex(*cargs))
+        ts.append(time.perf_counter() - t0)
+    res["fp64_64x64_latency_us_c_abi"] = float(np.median(ts) * 1e6)
+    res["fp64_64x64_m_s"] = [info.m, info.s]
+    t0 = time.perf_counter()
+    oracle.cossin(A)
+    res["fp64_64x64_oracle_us"] = (time.perf_counter() - t0) * 1e6
     res["fp64_64x64_rel_err_vs_oracle"] = max(
         float(np.linalg.norm(C.cpu().numpy() - Co) / np.linalg.norm(Co)),
         float(np.linalg.norm(S.cpu().numpy() - So) / np.linalg.norm(So)))

@@ -133,6 +133,9 @@ cs_status cossin_norm1(const void* A_dev, int64_t n, cs_prec prec, double* norm1
  *     until the process exits.
  *   - The first call on each device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
+ *     The address is kept for the life of the process: after a
+ *     cudaDeviceReset of that device the kept address is stale, so do not
+ *     call this entry point on that device again in the same process.
  *   - Every call on a device shares the one array, which keeps the last
  *     call's contents (the words that must start at zero are cleared on
  *     `stream` by each call).  Calls that overlap on the GPU (concurrent
@@ -205,6 +208,14 @@ cs_status cossin_cs(const void* A_dev, int64_t n, double t, cs_prec prec, void* 
  * CS_ETIMEOUT and clears the word; the context stays usable.  Returns CS_OK
  * once the kernel is queued on `stream`. */
 cs_status cossin_selftest_wait_timeout(cossin_stream_t stream);
+
+/* Measured FP64 FMA throughput of the current device (the paper has no
+ * counterpart): one register-only kernel, 16 independent FMA chains of
+ * `rounds` steps in each of 256 threads x 4 CTAs per SM, timed with CUDA
+ * events after a warm-up launch; *tflops = 2 x FMAs / time.  It is the
+ * denominator of the FP64 product kernel's roofline.  Blocks until done;
+ * allocates a small stream-ordered scratch. */
+cs_status cossin_fp64_fma_rate(int64_t rounds, double* tflops, cossin_stream_t stream);
 
 /* Allocation-failure self test (the paper has no counterpart): the next
  * `count` device allocations the library makes for itself (the workspaces of

@@ -286,6 +286,13 @@ def backward_workspace_size(count: int, n: int, max_s: int, prec: str = "fp64") 
     return int(out.value)
 
 
+def fp64_fma_rate(rounds: int = 16384, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double()
+    check(lib().cossin_fp64_fma_rate(int(rounds), ctypes.byref(out), _stream_ptr(stream)))
+    return float(out.value)
+
+
 def selftest_fail_next_alloc(count: int = 1) -> None:
     """Test hook: the library's next ``count`` device allocations fail (CS_ENOMEM)."""
     lib().cossin_selftest_fail_next_alloc(int(count))

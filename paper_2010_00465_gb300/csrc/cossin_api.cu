@@ -529,6 +529,9 @@ cs_status cossin_impl(const void* A, int64_t n, cs_prec prec, void* C, void* S, 
   if (!ws || ws_bytes < L.total) return fail(CS_EINVAL, "workspace missing or too small");
   if (((uintptr_t)ws & 255) != 0) return fail(CS_EINVAL, "workspace must be 256-byte aligned");
   char* w = (char*)ws;
+  // a single small FP64 matrix: one cooperative launch, (2m, s) chosen on the device
+  if (small_f64_eligible(prec, n))
+    return small_f64((const double*)A, n, (double*)C, (double*)S, w, L, force_m, force_s, info, stream, scale);
   double* nrm_dev = (double*)(w + L.norm_out);
   if (prec == CS_FP32)
     CS_CHECK(norm1_f32((const float*)A, n, (double*)(w + L.norm_partial), nrm_dev, stream));

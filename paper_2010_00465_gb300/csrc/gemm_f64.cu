@@ -20,6 +20,38 @@ namespace {
 
 constexpr int BK = 8, THREADS = 256;
 
+// The fused epilogue for entry (r, c) of a product with value p.
+__device__ __forceinline__ void epilogue_store(const Epilogue<double>& epi, int64_t eoff, int64_t r, int64_t c,
+                                               int64_t ldo, double p) {
+  if (epi.split_row >= 0) {
+    const bool top = r < epi.split_row;
+    const int64_t rr = top ? r : r - epi.split_row;
+    const int t = top ? 0 : 1;
+    epi.out[t][eoff + rr * ldo + c] = epi.alpha[t] * p + (rr == c ? epi.gamma[t] : 0.0);
+    return;
+  }
+  const int64_t idx = eoff + r * ldo + c;
+  double in[EPI_MAX_IN], o[EPI_MAX_OUT];
+#pragma unroll
+  for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
+#pragma unroll
+  for (int t = 0; t < EPI_MAX_OUT; ++t) {
+    if (t >= epi.n_out) break;
+    double v = epi.alpha[t] * p + (r == c ? epi.gamma[t] : 0.0);
+#pragma unroll
+    for (int q = 0; q < EPI_MAX_IN; ++q)
+      if (q < epi.n_in) v += epi.beta[t][q] * in[q];
+#pragma unroll
+    for (int u = 0; u < t; ++u) v += epi.delta[t][u] * o[u];
+    o[t] = v;
+  }
+#pragma unroll
+  for (int t = 0; t < EPI_MAX_OUT; ++t) {
+    if (t >= epi.n_out) break;
+    epi.out[t][idx] = o[t];
+  }
+}
+
 // TILE x TILE block tile (TILE = 128 or 64); thread (ty, tx) of 16 x 16 owns
 // rows {h*64 + ty*4 + i} and columns {h*64 + tx*4 + j}, h < TILE/64, i, j < 4.
 template <int TILE, bool TX, bool TY>
@@ -105,36 +137,42 @@ gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int6
     for (int j = 0; j < R; ++j) {
       const int64_t c = n0 + (j / 4) * 64 + tx * 4 + (j % 4);
       if (c >= N) continue;
-      const double p = acc[i][j];
-      if (epi.split_row >= 0) {
-        const bool top = r < epi.split_row;
-        const int64_t rr = top ? r : r - epi.split_row;
-        const int t = top ? 0 : 1;
-        epi.out[t][eoff + rr * ldo + c] = epi.alpha[t] * p + (rr == c ? epi.gamma[t] : 0.0);
-      } else {
-        const int64_t idx = eoff + r * ldo + c;
-        double in[EPI_MAX_IN], o[EPI_MAX_OUT];
-#pragma unroll
-        for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
-#pragma unroll
-        for (int t = 0; t < EPI_MAX_OUT; ++t) {
-          if (t >= epi.n_out) break;
-          double v = epi.alpha[t] * p + (r == c ? epi.gamma[t] : 0.0);
-#pragma unroll
-          for (int q = 0; q < EPI_MAX_IN; ++q)
-            if (q < epi.n_in) v += epi.beta[t][q] * in[q];
-#pragma unroll
-          for (int u = 0; u < t; ++u) v += epi.delta[t][u] * o[u];
-          o[t] = v;
-        }
-#pragma unroll
-        for (int t = 0; t < EPI_MAX_OUT; ++t) {
-          if (t >= epi.n_out) break;
-          epi.out[t][idx] = o[t];
-        }
-      }
+      epilogue_store(epi, eoff, r, c, ldo, acc[i][j]);
     }
   }
+}
+
+// Small products (a single matrix of order up to a few hundred has too few
+// 64-wide tiles to occupy the SMs, and each SM retires only two FP64 FMAs a
+// clock): TS x TS outputs per CTA, one per thread, k-slices of TS staged in
+// shared memory.
+template <int TS, bool TX, bool TY>
+__global__ void __launch_bounds__(TS * TS)
+gemm_f64_small_kernel(const double* __restrict__ X, const double* __restrict__ Y, int64_t M, int64_t N,
+                      int64_t K, int64_t ldx, int64_t ldy, int64_t ldo, int64_t bsx, int64_t bsy,
+                      int64_t bse, const Epilogue<double> epi) {
+  __shared__ double Xs[TS][TS + 1];  // [m][k]
+  __shared__ double Ys[TS][TS + 1];  // [k][n]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t m0 = (int64_t)blockIdx.y * TS, n0 = (int64_t)blockIdx.x * TS;
+  const int64_t b = blockIdx.z;
+  X += b * bsx;
+  Y += b * bsy;
+  double acc = 0.0;
+  for (int64_t k0 = 0; k0 < K; k0 += TS) {
+    {  // thread (ty, tx) loads op(X)[m0 + ty][k0 + tx] and op(Y)[k0 + ty][n0 + tx]
+      const int64_t gm = m0 + ty, gk = k0 + tx;
+      Xs[ty][tx] = (gm < M && gk < K) ? (TX ? X[gk * ldx + gm] : X[gm * ldx + gk]) : 0.0;
+      const int64_t gk2 = k0 + ty, gn = n0 + tx;
+      Ys[ty][tx] = (gk2 < K && gn < N) ? (TY ? Y[gn * ldy + gk2] : Y[gk2 * ldy + gn]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TS; ++kk) acc = fma(Xs[ty][kk], Ys[kk][tx], acc);
+    __syncthreads();
+  }
+  const int64_t r = m0 + ty, c = n0 + tx;
+  if (r < M && c < N) epilogue_store(epi, b * bse, r, c, ldo, acc);
 }
 
 }  // namespace
@@ -145,11 +183,36 @@ cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64
   if (M <= 0 || N <= 0 || batch <= 0) return CS_OK;
   // 128-wide tiles unless that leaves fewer than two waves of CTAs (small
   // batched products), where 64-wide tiles balance the SMs better.
-  const int64_t ctas128 = ((M + 127) / 128) * ((N + 127) / 128) * batch;
-  const int tile = ctas128 < 2 * 152 ? 64 : 128;
+  int dev = 0, sms = 0;
+  CS_CUDA_CHECK(cudaGetDevice(&dev));
+  CS_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // 128-wide tiles; 64-wide ones if that leaves fewer than two waves of
+  // CTAs; 16- or 8-wide single-output-per-thread tiles when even 64-wide
+  // tiles would leave most SMs idle (single matrices of small order).
+  auto ctas = [&](int t) { return ((M + t - 1) / t) * ((N + t - 1) / t) * batch; };
+  int tile = ctas(128) < 2 * (int64_t)sms ? 64 : 128;
+  if (tile == 64 && ctas(64) < sms / 2) tile = ctas(16) >= sms / 2 ? 16 : 8;
   if ((M + tile - 1) / tile > 65535 || batch > 65535) return fail(CS_EINVAL, "gemm_f64: grid too large");
   dim3 grid((unsigned)((N + tile - 1) / tile), (unsigned)((M + tile - 1) / tile), (unsigned)batch);
   ProfScope prof(CS_KERNEL_GEMM_F64, 2.0 * (double)M * (double)N * (double)K * (double)batch, stream);
+  if (tile <= 16) {
+#define CS_F64_SMALL(TS)                                                                                            \
+  {                                                                                                                 \
+    const dim3 blk(TS, TS);                                                                                         \
+    if (!transX && !transY)                                                                                         \
+      gemm_f64_small_kernel<TS, false, false><<<grid, blk, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi); \
+    else if (transX && !transY)                                                                                     \
+      gemm_f64_small_kernel<TS, true, false><<<grid, blk, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);  \
+    else if (!transX && transY)                                                                                     \
+      gemm_f64_small_kernel<TS, false, true><<<grid, blk, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);  \
+    else                                                                                                            \
+      gemm_f64_small_kernel<TS, true, true><<<grid, blk, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);   \
+  }
+    if (tile == 16) CS_F64_SMALL(16) else CS_F64_SMALL(8)
+#undef CS_F64_SMALL
+    CS_CUDA_CHECK(cudaGetLastError());
+    return CS_OK;
+  }
 #define CS_F64_LAUNCH(T)                                                                                           \
   if (!transX && !transY)                                                                                          \
     gemm_f64_kernel<T, false, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi); \
@@ -169,4 +232,58 @@ cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64
   return CS_OK;
 }
 
+namespace {
+
+// Register-only FP64 FMA throughput: every thread runs CH independent
+// dependency chains, so the FP64 pipes rather than latency set the rate.  The
+// multiplier and addend come in as arguments, so every FMA takes register
+// operands as the product kernels' do.
+template <int CH>
+__global__ void fma_rate_kernel(double* out, long long rounds, double b, double c) {
+  double a[CH];
+#pragma unroll
+  for (int i = 0; i < CH; ++i) a[i] = 1.0 + 1e-3 * i + 1e-9 * threadIdx.x;
+  for (long long r = 0; r < rounds; ++r) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) a[i] = fma(a[i], b, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < CH; ++i) sum += a[i];
+  if (sum == 12345.678) out[blockIdx.x] = sum;  // never true; keeps the chains live
+}
+
+}  // namespace
+
 }  // namespace cs
+
+extern "C" cs_status cossin_fp64_fma_rate(int64_t rounds, double* tflops, cossin_stream_t stream) {
+  using namespace cs;
+  if (!tflops) return fail(CS_EINVAL, "tflops is null");
+  if (rounds <= 0 || rounds > (int64_t(1) << 30)) return fail(CS_EINVAL, "rounds must be in [1, 2^30]");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  CS_CUDA_CHECK(cudaGetDevice(&dev));
+  CS_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = sms * 4;
+  double* out = nullptr;
+  CS_CHECK(dev_alloc((void**)&out, sizeof(double) * grid, st, "cossin_fp64_fma_rate scratch"));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cs_status rc = CS_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = fail(CS_ECUDA, "cudaEventCreate");
+  if (rc == CS_OK) {
+    fma_rate_kernel<16><<<grid, 256, 0, st>>>(out, rounds / 8 + 1, 0.9999999, 1e-9);  // warm-up
+    cudaEventRecord(e0, st);
+    fma_rate_kernel<16><<<grid, 256, 0, st>>>(out, rounds, 0.9999999, 1e-9);
+    cudaEventRecord(e1, st);
+    const cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "fma_rate_kernel");
+    else if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f) rc = fail(CS_ECUDA, "event timing failed");
+    else *tflops = 2.0 * 16.0 * (double)rounds * 256.0 * grid / (ms * 1e-3) / 1e12;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(out, st);
+  return rc;
+}

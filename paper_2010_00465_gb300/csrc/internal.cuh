@@ -148,6 +148,11 @@ cs_status backward_impl(int64_t count, int64_t n, double scale, const double* A,
                         size_t ws_bytes = 0);
 size_t backward_workspace_bytes(int64_t count, int64_t n, int max_s, bool emu);
 cs_status check_prec(cs_prec prec);
+// One small FP64 matrix (n <= 128) in a single cooperative launch (small_f64.cu).
+struct Layout;
+bool small_f64_eligible(cs_prec prec, int64_t n);
+cs_status small_f64(const double* A, int64_t n, double* C, double* S, char* ws, const Layout& L, int32_t force_m,
+                    int32_t force_s, cs_info* info, cudaStream_t stream, double scale);
 // Every precision keeps FP64 intermediates.  uses_emu: some products are
 // sliced BF16 tensor-core products (CS_FP64_EMU, CS_SPLIT_EMU, CS_SPLIT_BF16,
 // CS_FP32); f64_operands: every product takes FP64 operands (all but the TF32

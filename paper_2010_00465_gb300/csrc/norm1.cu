@@ -296,7 +296,3 @@ extern "C" cs_status cossin_norm1_noalloc(const void* A, int64_t n, cs_prec prec
   if (prec == CS_FP32) return cs::norm1_f32((const float*)A, n, scratch, norm1_dev, st);
   return cs::norm1_f64((const double*)A, n, scratch, norm1_dev, st);
 }
-
-namespace cs {
-
-}  // namespace cs
