@@ -79,9 +79,9 @@ constexpr int kFloatsPerN2 = 2 * kDfSlots + 4;  // + two stacked FP32 [C; S] buf
 // columns, so NT = 128 runs one CTA per SM and NT = 64 two.  The epilogue
 // stages a tile's product (two planes of 128 x NT floats) in the stages,
 // which are idle once the tile's MMAs are done.
-template <int NT>
+template <int NT, int TH>
 struct Cfg {
-  static constexpr int kThreads = NT == 128 ? 512 : 256;  // 512 threads per SM either way
+  static constexpr int kThreads = TH;
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kABytes = kBM * kKc * 2;  // one A slice of a stage
   static constexpr int kBBytes = NT * kKc * 2;   // one B slice of a stage
@@ -355,10 +355,10 @@ __device__ void prepass(const Opnd& X, const Opnd& Y, int M, int N, int K, int n
 // warp covers 8 x 8 blocks, a word (two k) per lane: the 32 words of a block
 // and slice fall on distinct banks.  A warp loads every element of its
 // blocks before it converts any, so the loads are in flight together.
-template <int NT>
+template <int NT, int TH>
 __device__ void slice_chunk(const Opnd& X, const Opnd& Y, int m0, int n0, int M, int N, int n16, int K, int k0,
                             int n, const Shared& sh, uint8_t* stA, uint8_t* stB) {
-  using C = Cfg<NT>;
+  using C = Cfg<NT, TH>;
   constexpr int kWarps = C::kWarps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kAB = (kBM / 8) * 4 / kWarps;  // A blocks per warp
@@ -513,10 +513,10 @@ __device__ __forceinline__ void finish(const Opnd& Y, const Mat& m, const Epi& e
 }
 
 // One product P = X Y (M x N, inner K = n) of matrix m with its epilogue.
-template <int NT>
+template <int NT, int TH>
 __device__ bool product(const Opnd& X, const Opnd& Y, int M, int N, int K, const Mat& m, const Epi& ep,
                         Shared& sh, uint8_t* smem, Pipe& pipe) {
-  using C = Cfg<NT>;
+  using C = Cfg<NT, TH>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = m.n;
   prepass<C::kWarps>(X, Y, M, N, K, n, sh);
@@ -537,7 +537,7 @@ __device__ bool product(const Opnd& X, const Opnd& Y, int M, int N, int K, const
         if (sh.abort_flag) return false;
         uint8_t* stA = smem + st * C::kStageBytes;
         uint8_t* stB = stA + kSlices * C::kABytes;
-        slice_chunk<NT>(X, Y, m0, n0, M, N, n16, K, kc * kKc, n, sh, stA, stB);
+        slice_chunk<NT, TH>(X, Y, m0, n0, M, N, n16, K, kc * kKc, n, sh, stA, stB);
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -642,11 +642,11 @@ __device__ bool product(const Opnd& X, const Opnd& Y, int M, int N, int K, const
   return true;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(Cfg<NT>::kThreads, Cfg<NT>::kCtasPerSm)
+template <int NT, int TH>
+__global__ void __launch_bounds__(TH, Cfg<NT, TH>::kCtasPerSm)
     batched_kernel(const Desc* __restrict__ desc, const int* __restrict__ order, int count, int* queue,
                    float* ws_all, int64_t ws_per_cta, cs_info* infos, int32_t* status, int* err) {
-  using C = Cfg<NT>;
+  using C = Cfg<NT, TH>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ Shared sh;
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(Cfg<NT>::kThreads, Cfg<NT>::kCtasPerSm)
     const DPlan& P = c_plans[f];
     for (int k = 0; k < P.nsteps && ok; ++k) {
       const Opnd X = slot_opnd(P.step[k].X), Y = slot_opnd(P.step[k].Y);
-      ok = product<NT>(X, Y, n, n, n, m, Epi{f, k, nullptr, nullptr}, sh, smem, pipe);
+      ok = product<NT, TH>(X, Y, n, n, n, m, Epi{f, k, nullptr, nullptr}, sh, smem, pipe);
     }
     // double-angle steps: the first reads the chain's double-float C and S,
     // the others the FP32 stacked buffers ping[0], ping[1]
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(Cfg<NT>::kThreads, Cfg<NT>::kCtasPerSm)
       }
       float* nxt = (q & 1) ? ping1 : ping0;
       const bool last = q == s - 1;
-      ok = product<NT>(X, Y, 2 * n, n, n, m, Epi{0, -1, last ? d.C : nxt, last ? d.S : nxt + m.n2}, sh, smem, pipe);
+      ok = product<NT, TH>(X, Y, 2 * n, n, n, m, Epi{0, -1, last ? d.C : nxt, last ? d.S : nxt + m.n2}, sh, smem, pipe);
     }
     if (!ok) break;
   }
@@ -765,12 +765,13 @@ __global__ void __launch_bounds__(Cfg<NT>::kThreads, Cfg<NT>::kCtasPerSm)
 struct Variant {
   int tile;  // output tile columns (N of each MMA, at most)
   int ctas_per_sm;
+  int threads;
 };
 // Tiles of 128 x 128 (four level accumulators fill TMEM's 512 columns, one
-// CTA per SM) or 128 x 64 (half of TMEM, two CTAs per SM, so one CTA's
-// slicing and epilogue overlap the other's MMAs; orders above 64 take twice
-// the tiles): the autotuner keeps whichever is faster on the batch.
-const Variant kVariants[] = {{128, 1}, {64, 2}};
+// CTA of 512 threads per SM) or 128 x 64 (half of TMEM, two CTAs per SM, of
+// 256 or 512 threads; orders above 64 take twice the tiles): the autotuner
+// keeps whichever is fastest on the batch.
+const Variant kVariants[] = {{128, 1, 512}, {64, 2, 256}, {64, 2, 512}};
 
 std::mutex g_mu;
 bool g_plans_uploaded[64] = {};
@@ -861,12 +862,12 @@ BLayout make_blayout(int64_t count, int64_t nmax) {
   return L;
 }
 
-template <int NT>
+template <int NT, int TH>
 cs_status launch_tile(int grid, const BLayout& L, char* ws, int count, cs_info* infos, int32_t* status, int* err,
                       cudaStream_t stream) {
   static std::atomic<unsigned long long> smem_set{0};
-  CS_CHECK(smem_limit_once(batched_kernel<NT>, Cfg<NT>::kSmem, smem_set));
-  batched_kernel<NT><<<grid, Cfg<NT>::kThreads, Cfg<NT>::kSmem, stream>>>(
+  CS_CHECK(smem_limit_once(batched_kernel<NT, TH>, Cfg<NT, TH>::kSmem, smem_set));
+  batched_kernel<NT, TH><<<grid, TH, Cfg<NT, TH>::kSmem, stream>>>(
       (const Desc*)(ws + L.desc), (const int*)(ws + L.order), count, (int*)(ws + L.queue),
       (float*)(ws + L.scratch), L.per_cta, infos, status, err);
   CS_CUDA_CHECK(cudaGetLastError());
@@ -880,8 +881,9 @@ cs_status launch_variant(int v, const BLayout& L, char* ws, int count, cs_info* 
   int* err = tc_error_word();
   if (!err) return fail(CS_ECUDA, "cannot resolve the device error word");
   CS_CUDA_CHECK(cudaMemsetAsync(ws + L.queue, 0, sizeof(int), stream));
-  if (V.tile == 128) return launch_tile<128>(grid, L, ws, count, infos, status, err, stream);
-  return launch_tile<64>(grid, L, ws, count, infos, status, err, stream);
+  if (V.tile == 128) return launch_tile<128, 512>(grid, L, ws, count, infos, status, err, stream);
+  if (V.threads == 512) return launch_tile<64, 512>(grid, L, ws, count, infos, status, err, stream);
+  return launch_tile<64, 256>(grid, L, ws, count, infos, status, err, stream);
 }
 
 }  // namespace bt
