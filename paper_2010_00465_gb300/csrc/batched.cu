@@ -530,16 +530,17 @@ __device__ bool product(const Opnd& X, const Opnd& Y, int M, int N, int K, const
       for (int kc = 0; kc < nchunks; ++kc) {
         const int g = pipe.chunks;
         const int st = g & 1;
-        // the stage was last read by chunk g - 2
+        // The stage was last read by chunk g - 2: every thread waits for that
+        // commit itself, so the threads slice chunk g while thread 0 may
+        // still be issuing chunk g - 1's MMAs.
         if (g >= 2 && !mbar_wait(&sh.mma_bar[st], ((g - 2) >> 1) & 1, (volatile int*)&sh.abort_flag))
           sh.abort_flag = 1;
-        __syncthreads();
-        if (sh.abort_flag) return false;
         uint8_t* stA = smem + st * C::kStageBytes;
         uint8_t* stB = stA + kSlices * C::kABytes;
         slice_chunk<NT, TH>(X, Y, m0, n0, M, N, n16, K, kc * kKc, n, sh, stA, stB);
         fence_async_smem();
         __syncthreads();
+        if (sh.abort_flag) return false;
         if (threadIdx.x == 0) {
           tc_fence_after();
           // descriptors: start address >> 4, LBO 1 (unused), SBO 512 bytes
