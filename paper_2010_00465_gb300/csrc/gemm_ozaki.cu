@@ -57,17 +57,23 @@
 //   warp 1     allocates 512 TMEM columns (8 level accumulators of 64
 //              columns; two sets of 4 for S = 4) and issues the MMAs
 //              (cta_group::1, M = 128, K = 16):
-//              per slice p of A, N = 128 instructions that pair the slices q,
-//              q + 1 of B into the accumulators of levels p + q, p + q + 1
-//              (16 per k-step, plus 4 of N = 64 for the odd pair left), the
-//              p = 0 instructions restarting every accumulator at a chunk
-//              start once the epilogue has read it;
+//              per slice p of A, N = 256, 128 and 64 instructions that take
+//              4, 2 or 1 adjacent slices q, q + 1, ... of B into the
+//              accumulators of levels p + q, p + q + 1, ... (14 per k-step
+//              for S = 8, 5 for S = 4), the p = 0 instructions restarting
+//              every accumulator at a chunk start once the epilogue has read
+//              it;
 //   warps 2-9  two per TMEM lane quarter, 32 columns each: after each chunk,
 //              read every accumulator (freeing it at once), add it into the
-//              int64 sums; at the end stage the tile through the (then idle)
-//              shared memory and run the FP64 epilogue row by row with
-//              coalesced loads and stores (a thread-per-row epilogue took a
-//              fifth of the kernel's time).
+//              int64 sums; at the end of a tile write the sums (as FP64) to
+//              one of two scratch slots of the CTA in global memory (L2) and
+//              go on with the next tile's chunks;
+//   warps 10-13 the FP64 epilogue of each tile from its scratch slot, row
+//              by row with coalesced loads and stores, while the next tile's
+//              MMAs and drains run (done by the draining warps, it held the
+//              MMAs up at the next tile's first chunk boundaries: a quarter
+//              of the eight-slice kernel's time, two fifths of the
+//              four-slice one's).
 // Every mbarrier wait is bounded; on expiry the CTA stops issuing, waits
 // (bounded) for what it issued, frees TMEM and raises *err.
 #include <cuda.h>
@@ -92,16 +98,15 @@ constexpr int BN = 64;
 // 4 stages measured 5 % slower), 64 for four slices (128-byte swizzle,
 // 2 stages of 96 KB).
 __host__ __device__ constexpr int stage_k(int S) { return S == kOzakiSlicesSplit ? 64 : 32; }
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiWarps = 8;  // drain TMEM into the int64 sums
+constexpr int kFinWarps = 4;  // FP64 epilogue
+constexpr int kThreads = 64 + 32 * (kEpiWarps + kFinWarps);
 constexpr int kCols = BN / 2;          // columns per epilogue warp
 constexpr int kGroupM = 8;             // M tiles per raster group
 // TMA boxes of 256 rows: a tile's slices lie next to each other in global
 // memory (and in a stage), so one box carries two A slices (2 x 128 rows) or
 // four B slices (4 x 64 rows): 6 loads per stage instead of 16 for S = 8.
 constexpr int kBoxRows = 256;
-constexpr int kStageRows = 32;          // rows of the tile staged per epilogue round
-constexpr int kLd = 2 * kCols + 1;      // staging row pitch (doubles)
 // Per slice count S: all S slices of A and B^T of one k-block form a stage,
 // 192 KB of stages are in flight, and the S level accumulators of BN columns
 // fill S BN TMEM columns.
@@ -110,22 +115,45 @@ __host__ __device__ constexpr int b_slice_bytes(int S) { return BN * stage_k(S) 
 __host__ __device__ constexpr int stage_bytes(int S) { return S * (a_slice_bytes(S) + b_slice_bytes(S)); }
 __host__ __device__ constexpr int num_stages(int S) { return (192 * 1024) / stage_bytes(S); }
 __host__ __device__ constexpr int smem_bytes(int S) {
-  return num_stages(S) * stage_bytes(S) + kStageRows * kLd * 8 + 1024;  // stages + epilogue staging
+  return num_stages(S) * stage_bytes(S) + 1024;
 }
 static_assert(smem_bytes(kOzakiSlices) <= 227 * 1024 && smem_bytes(kOzakiSlicesSplit) <= 227 * 1024,
               "shared memory");
 static_assert(kOzakiSlices * BN == 512 && kOzakiSlicesSplit * BN == 256, "TMEM columns: a power of two <= 512");
 // Instruction descriptors, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-// An N = 2 BN instruction reads the B slices q and q + 1, which lie next to
-// each other along N in shared memory, and writes the accumulators of levels
-// p + q and p + q + 1, which lie next to each other in TMEM: two slice pairs
-// per instruction (a 128 x 64 x 16 MMA runs at 2/3 of the tensor peak on
-// GB300, 128 x 128 x 16 at the peak).
+// An N = w BN instruction reads the B slices q .. q + w - 1, which lie next
+// to each other along N in shared memory, and writes the accumulators of
+// levels p + q .. p + q + w - 1, which lie next to each other in TMEM: w
+// slice pairs per instruction (a 128 x 64 x 16 MMA runs at 2/3 of the tensor
+// peak on GB300, 128 x 128 x 16 at the peak), and A is read once per w pairs.
 constexpr uint32_t kIdesc1 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 constexpr uint32_t kIdesc2 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t kIdesc4 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((4 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// The slice products of A slice p: B slices q = 0 .. S - 1 - p in groups of
+// 4, 2 and 1 adjacent slices (group grp starts at group_start, spans
+// group_width, 0 past the last), one instruction each; a wider instruction
+// reads the A operand from shared memory once for more slice pairs.
+__host__ __device__ constexpr int group_width(int S, int p, int grp) {
+  int q = 0, w = 0;
+  for (int i = 0; i <= grp; ++i) {
+    q += w;
+    const int left = S - p - q;
+    w = left >= 4 ? 4 : left >= 2 ? 2 : left >= 1 ? 1 : 0;
+  }
+  return w;
+}
+__host__ __device__ constexpr int group_start(int S, int p, int grp) {
+  int q = 0;
+  for (int i = 0; i < grp; ++i) q += group_width(S, p, i);
+  return q;
+}
+static_assert(group_width(8, 1, 0) == 4 && group_width(8, 1, 1) == 2 && group_width(8, 1, 2) == 1 &&
+                  group_start(8, 1, 2) == 6 && group_width(8, 0, 2) == 0 && group_width(4, 3, 0) == 1,
+              "slice groups");
 
 // Shared-memory descriptors (built in the MMA loop): K-major, 64-byte
 // swizzle, rows of 64 bytes, 8-row (512-byte) atoms stacked along M/N
@@ -318,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const double* __restrict__ X_all, int64_t ldx, const double* __restrict__ Y_all, int64_t ldy,
                  const double* __restrict__ xd_all, const double* __restrict__ yd_all, int64_t ldo,
                  const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse,
-                 int batch) {
+                 int batch, double* __restrict__ hand) {
   constexpr int kAcc = S;  // one accumulator of BN columns per level p + q < S
   constexpr int BK = stage_k(S);
   constexpr int kSwizzleBytes = BK * 2;  // one swizzle row = one stage row
@@ -334,14 +362,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t kTmemCols = (uint32_t)(S * BN * kBufs);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  double* stage_tile = (double*)(smem + kStages * kStageBytes);  // kStageRows x kLd doubles
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
   __shared__ __align__(8) uint64_t chunk_bar[kBufs];
   __shared__ __align__(8) uint64_t free_bar[kBufs][kAcc];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  __shared__ int stop_epi;
+  __shared__ __align__(8) uint64_t hand_full[2];  // a tile's sums are in scratch slot t % 2
+  __shared__ __align__(8) uint64_t hand_free[2];  // the FP64 epilogue is done with the slot
   __shared__ int kb_consumed;
   __shared__ int chunks_committed;
 
@@ -373,7 +401,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int a = 0; a < kAcc; ++a) mbar_init(&free_bar[b][a], kEpiWarps);
     }
     abort_flag = 0;
-    stop_epi = 0;
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&hand_full[h], kEpiWarps);
+      mbar_init(&hand_free[h], kFinWarps);
+    }
     kb_consumed = 0;
     chunks_committed = 0;
     fence_mbar_init();
@@ -452,32 +483,34 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int p = 0; p < S; ++p) {
                 const uint64_t ad =
                     ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
-                // pairs (p, q), (p, q + 1) for q = 0, 2, ...: levels p + q, p + q + 1 < S
+                // B slices q .. q + w - 1 in one N = w BN instruction into
+                // the accumulators of levels p + q .. p + q + w - 1 < S
 #pragma unroll
-                for (int q = 0; p + q + 1 < S; q += 2) {
+                for (int grp = 0; grp < 3; ++grp) {
+                  const int w = group_width(S, p, grp);
+                  if (w == 0) break;
+                  const int q = group_start(S, p, grp);
                   const uint64_t bd =
                       ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
                   // p = 0 touches every level first: there a chunk restarts
                   // its accumulators, after the epilogue has read them
                   const bool restart = chunk_start && j == 0 && p == 0;
                   if (restart && wait_free) {
-                    if (!mbar_wait(&free_bar[buf][q], free_par, &abort_flag) ||
-                        !mbar_wait(&free_bar[buf][q + 1], free_par, &abort_flag)) {
+                    bool freed = true;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                      if (l < w) freed = freed && mbar_wait(&free_bar[buf][q + l], free_par, &abort_flag);
+                    if (!freed) {
                       abort_flag = 1;
                       stop = true;
                       break;
                     }
                     tc_fence_after();
                   }
-                  mma_bf16(acc0 + (uint32_t)((p + q) * BN), ad, bd, kIdesc2, restart ? 0u : 1u);
+                  mma_bf16(acc0 + (uint32_t)((p + q) * BN), ad, bd, w == 4 ? kIdesc4 : w == 2 ? kIdesc2 : kIdesc1,
+                           restart ? 0u : 1u);
                 }
                 if (stop) break;
-                if ((S - p) & 1) {  // the last pair (p, S - 1 - p) alone, level S - 1
-                  const int q = S - 1 - p;
-                  const uint64_t bd =
-                      ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
-                  mma_bf16(acc0 + (uint32_t)((S - 1) * BN), ad, bd, kIdesc1, 1u);
-                }
               }
             }
             if (stop) break;
@@ -489,15 +522,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else {
+  } else if (warp < 2 + kEpiWarps) {
     const int quarter = warp & 3;                // TMEM lanes 32*quarter .. +31
     const int col0 = ((warp - 2) >> 2) * kCols;  // this warp's 32 columns
-    const int we = warp - 2;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     int cg = 0;  // chunks drained so far, over all tiles
-    for (int u = blockIdx.x; u < total; u += gridDim.x) {
-      int bat, m0, n0;
-      tile_of(u, bat, m0, n0);
+    int t = 0;   // tiles handed over so far
+    for (int u = blockIdx.x; u < total; u += gridDim.x, ++t) {
       // Fixed-point sums with quantum 2^-35 of the slice products: each
       // chunk's level-L value (L <= 5) is an integer multiple of 2^(-7L) below
       // 2^24 quanta and converts exactly; levels 6, 7 are rounded to 2^-35.
@@ -538,79 +569,97 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      // FP64 epilogue, one quarter of the tile (32 rows) at a time: the two
-      // warps holding it stage their sums, then all eight walk its rows with
-      // coalesced loads and stores.
+      // Hand the sums to the finishing warps through this CTA's scratch slot
+      // t % 2, once they are done with tile t - 2 there, and go on to the
+      // next tile's chunks.
+      if (ok && t >= 2) {
+        int w = 1;
+        if (lane == 0) {
+          w = mbar_wait(&hand_free[t & 1], ((t >> 1) - 1) & 1, &abort_flag) && !abort_flag;
+          if (!w) abort_flag = 1;
+        }
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+      }
+      if (!ok) break;
+      double* __restrict__ hrow = hand + ((int64_t)(blockIdx.x * 2 + (t & 1)) * BM + quarter * 32 + lane) * BN + col0;
+#pragma unroll
+      for (int j = 0; j < kCols; j += 2)
+        *reinterpret_cast<double2*>(hrow + j) = make_double2((double)acc[j], (double)acc[j + 1]);
+      __threadfence();  // the sums reach L2, where the finishing warps read them
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&hand_full[t & 1]);
+    }
+  } else {
+    // FP64 epilogue of each tile from its scratch slot: warp fw walks rows
+    // fw, fw + kFinWarps, ... with coalesced loads and stores.
+    const int fw = warp - 2 - kEpiWarps;
+    int t = 0;
+    for (int u = blockIdx.x; u < total; u += gridDim.x, ++t) {
+      int w = 1;
+      if (lane == 0) {
+        w = mbar_wait(&hand_full[t & 1], (t >> 1) & 1, &abort_flag) && !abort_flag;
+        if (!w) abort_flag = 1;
+      }
+      if (!__shfl_sync(0xffffffffu, w, 0)) break;
+      int bat, m0, n0;
+      tile_of(u, bat, m0, n0);
       const int* __restrict__ ex = ex_all + (int64_t)bat * Mpad;
       const int* __restrict__ fx = fx_all + (int64_t)bat * Npad;
       const double* __restrict__ xd = xd_all + (int64_t)bat * Mpad;
       const double* __restrict__ yd = yd_all + (int64_t)bat * Npad;
       const double* __restrict__ X = X_all + (int64_t)bat * bsx;
       const double* __restrict__ Y = Y_all + (int64_t)bat * bsy;
+      const double* __restrict__ hslot = hand + (int64_t)(blockIdx.x * 2 + (t & 1)) * BM * BN;
       const int64_t eoff = (int64_t)bat * bse;
 #pragma unroll 1
-      for (int qr = 0; qr < 4; ++qr) {
-        if (quarter == qr && ok) {
+      for (int rl = fw; rl < BM; rl += kFinWarps) {
+        const int r = m0 + rl;
+        if (r >= M) break;
+        const int er = ex[r] - 14 - 35;
+        const int d = r % K;
+        const double xdr = xd[r];
+        const double* __restrict__ yrow = Y + (int64_t)d * ldy;
+        const double* __restrict__ xrow = X + (int64_t)r * ldx;
 #pragma unroll
-          for (int j = 0; j < kCols; ++j) stage_tile[lane * kLd + col0 + j] = (double)acc[j];
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
-        if (we == 0 && lane == 0) stop_epi = abort_flag;
-        if (!abort_flag) {
-#pragma unroll 1
-          for (int rq = we; rq < kStageRows; rq += kEpiWarps) {
-            const int rl = qr * kStageRows + rq;
-            const int r = m0 + rl;
-            if (r >= M) break;
-            const int er = ex[r] - 14 - 35;
-            const int d = r % K;
-            const double xdr = xd[r];
-            const double* __restrict__ yrow = Y + (int64_t)d * ldy;
-            const double* __restrict__ xrow = X + (int64_t)r * ldx;
+        for (int h = 0; h < BN / 32; ++h) {
+          const int cl = 32 * h + lane;
+          const int cc = n0 + cl;
+          if (cc >= N) continue;
+          // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
+          const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
+          const double p = fma(__ldcg(hslot + rl * BN + cl), pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
+          if (epi.split_row >= 0) {
+            const bool top = r < epi.split_row;
+            const int64_t rr = top ? r : r - epi.split_row;
+            const int o = top ? 0 : 1;
+            epi.out[o][eoff + rr * ldo + cc] = epi.alpha[o] * p + (rr == cc ? epi.gamma[o] : 0.0);
+          } else {
+            const int64_t idx = eoff + (int64_t)r * ldo + cc;
+            double in[EPI_MAX_IN], o[EPI_MAX_OUT];
 #pragma unroll
-            for (int h = 0; h < BN / 32; ++h) {
-              const int cl = 32 * h + lane;
-              const int cc = n0 + cl;
-              if (cc >= N) continue;
-              // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
-              const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
-              const double p = fma(stage_tile[rq * kLd + cl], pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
-              if (epi.split_row >= 0) {
-                const bool top = r < epi.split_row;
-                const int64_t rr = top ? r : r - epi.split_row;
-                const int t = top ? 0 : 1;
-                epi.out[t][eoff + rr * ldo + cc] = epi.alpha[t] * p + (rr == cc ? epi.gamma[t] : 0.0);
-              } else {
-                const int64_t idx = eoff + (int64_t)r * ldo + cc;
-                double in[EPI_MAX_IN], o[EPI_MAX_OUT];
+            for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
 #pragma unroll
-                for (int q = 0; q < EPI_MAX_IN; ++q) in[q] = q < epi.n_in ? epi.in[q][idx] : 0.0;
+            for (int t2 = 0; t2 < EPI_MAX_OUT; ++t2) {
+              if (t2 >= epi.n_out) break;
+              double v = epi.alpha[t2] * p + (r == cc ? epi.gamma[t2] : 0.0);
 #pragma unroll
-                for (int t = 0; t < EPI_MAX_OUT; ++t) {
-                  if (t >= epi.n_out) break;
-                  double v = epi.alpha[t] * p + (r == cc ? epi.gamma[t] : 0.0);
+              for (int q = 0; q < EPI_MAX_IN; ++q)
+                if (q < epi.n_in) v += epi.beta[t2][q] * in[q];
 #pragma unroll
-                  for (int q = 0; q < EPI_MAX_IN; ++q)
-                    if (q < epi.n_in) v += epi.beta[t][q] * in[q];
+              for (int uu = 0; uu < EPI_MAX_OUT; ++uu)
+                if (uu < t2) v += epi.delta[t2][uu] * o[uu];
+              o[t2] = v;
+            }
 #pragma unroll
-                  for (int uu = 0; uu < EPI_MAX_OUT; ++uu)
-                    if (uu < t) v += epi.delta[t][uu] * o[uu];
-                  o[t] = v;
-                }
-#pragma unroll
-                for (int t = 0; t < EPI_MAX_OUT; ++t) {
-                  if (t >= epi.n_out) break;
-                  epi.out[t][idx] = o[t];
-                }
-              }
+            for (int t2 = 0; t2 < EPI_MAX_OUT; ++t2) {
+              if (t2 >= epi.n_out) break;
+              epi.out[t2][idx] = o[t2];
             }
           }
         }
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
       }
-      // every epilogue warp reads the same stop flag (written before the
-      // last barrier), so all of them leave the tile loop together
-      if (stop_epi) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&hand_free[t & 1]);
     }
   }
 
@@ -695,7 +744,15 @@ OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch, int slices)
   d.colmax_bytes = al(nb * sizeof(unsigned long long) * (size_t)d.Npad);
   d.xd_bytes = al(nb * sizeof(double) * (size_t)d.Mpad);
   d.yd_bytes = al(nb * sizeof(double) * (size_t)d.Npad);
-  d.total = d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes + d.colmax_bytes + d.xd_bytes + d.yd_bytes;
+  // two tiles of sums per persistent CTA (at most one CTA per SM)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    sms = 256;
+  const int64_t tiles = (int64_t)nb * (d.Mpad / BM) * (d.Npad / BN);
+  d.hand_ctas = (int)std::min<int64_t>(tiles, sms);
+  d.hand_bytes = al((size_t)d.hand_ctas * 2 * BM * BN * sizeof(double));
+  d.total = d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes + d.colmax_bytes + d.xd_bytes + d.yd_bytes + d.hand_bytes;
   return d;
 }
 
@@ -715,6 +772,7 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   unsigned long long* colmax = (unsigned long long*)(w + d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes);
   double* xd = (double*)((char*)colmax + d.colmax_bytes);
   double* yd = (double*)((char*)xd + d.xd_bytes);
+  double* hand = (double*)((char*)yd + d.yd_bytes);
   const unsigned nb = (unsigned)batch;
   {
     ProfScope prof(CS_KERNEL_OTHER, (double)batch * (double)(M * K + K * N) * (8.0 + 2.0 * S), stream);
@@ -741,10 +799,10 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   int sms = 0, dev = 0;
   CS_CUDA_CHECK(cudaGetDevice(&dev));
   CS_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms > 0 ? sms : 1);
+  const unsigned grid = (unsigned)std::min<int64_t>(std::min<int64_t>(tiles, sms > 0 ? sms : 1), d.hand_ctas);
   ozaki_kernel<S><<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex,
                                                      fx, X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse,
-                                                     (int)batch);
+                                                     (int)batch, hand);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
