@@ -68,12 +68,14 @@
 //              int64 sums; at the end of a tile write the sums (as FP64) to
 //              one of two scratch slots of the CTA in global memory (L2) and
 //              go on with the next tile's chunks;
-//   warps 10-13 the FP64 epilogue of each tile from its scratch slot, row
+//   warps 10-17 the FP64 epilogue of each tile from its scratch slot, row
 //              by row with coalesced loads and stores, while the next tile's
 //              MMAs and drains run (done by the draining warps, it held the
 //              MMAs up at the next tile's first chunk boundaries: a quarter
 //              of the eight-slice kernel's time, two fifths of the
-//              four-slice one's).
+//              four-slice one's; four warps still held up the four-slice
+//              kernel, as the epilogue's FP64 operations are long-latency
+//              on GB300).
 // Every mbarrier wait is bounded; on expiry the CTA stops issuing, waits
 // (bounded) for what it issued, frees TMEM and raises *err.
 #include <cuda.h>
@@ -99,7 +101,7 @@ constexpr int BN = 64;
 // 2 stages of 96 KB).
 __host__ __device__ constexpr int stage_k(int S) { return S == kOzakiSlicesSplit ? 64 : 32; }
 constexpr int kEpiWarps = 8;  // drain TMEM into the int64 sums
-constexpr int kFinWarps = 4;  // FP64 epilogue
+constexpr int kFinWarps = 8;  // FP64 epilogue
 constexpr int kThreads = 64 + 32 * (kEpiWarps + kFinWarps);
 constexpr int kCols = BN / 2;          // columns per epilogue warp
 constexpr int kGroupM = 8;             // M tiles per raster group
@@ -611,6 +613,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double* __restrict__ Y = Y_all + (int64_t)bat * bsy;
       const double* __restrict__ hslot = hand + (int64_t)(blockIdx.x * 2 + (t & 1)) * BM * BN;
       const int64_t eoff = (int64_t)bat * bse;
+      // a plain product (one output, P itself) skips the linear combination
+      const bool plain = epi.split_row < 0 && epi.n_out == 1 && epi.n_in == 0 && epi.alpha[0] == 1.0 &&
+                         epi.gamma[0] == 0.0;
 #pragma unroll 1
       for (int rl = fw; rl < BM; rl += kFinWarps) {
         const int r = m0 + rl;
@@ -628,11 +633,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
           const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
           const double p = fma(__ldcg(hslot + rl * BN + cl), pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
-          if (epi.split_row >= 0) {
+          if (plain) {
+            epi.out[0][eoff + (int64_t)r * ldo + cc] = p;
+          } else if (epi.split_row >= 0) {
             const bool top = r < epi.split_row;
             const int64_t rr = top ? r : r - epi.split_row;
             const int o = top ? 0 : 1;
-            epi.out[o][eoff + rr * ldo + cc] = epi.alpha[o] * p + (rr == cc ? epi.gamma[o] : 0.0);
+            epi.out[o][eoff + rr * ldo + cc] = fma(epi.alpha[o], p, rr == cc ? epi.gamma[o] : 0.0);
           } else {
             const int64_t idx = eoff + (int64_t)r * ldo + cc;
             double in[EPI_MAX_IN], o[EPI_MAX_OUT];
@@ -641,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int t2 = 0; t2 < EPI_MAX_OUT; ++t2) {
               if (t2 >= epi.n_out) break;
-              double v = epi.alpha[t2] * p + (r == cc ? epi.gamma[t2] : 0.0);
+              double v = fma(epi.alpha[t2], p, r == cc ? epi.gamma[t2] : 0.0);
 #pragma unroll
               for (int q = 0; q < EPI_MAX_IN; ++q)
                 if (q < epi.n_in) v += epi.beta[t2][q] * in[q];
