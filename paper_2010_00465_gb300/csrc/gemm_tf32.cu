@@ -17,9 +17,12 @@
 //     accumulators, so the small terms are not truncated against the large
 //     sum; the corrections (2^-11 of the main term) accumulate over the whole
 //     K, where their own truncation stays far below FP32 rounding of the sum;
-//   * starts a fresh main accumulator every kGroup k-blocks (32 k) and
+//   * starts a fresh main accumulator every kGroup k-blocks (128 k) and
 //     promotes it into Kahan-compensated FP32 register sums (two TMEM buffers
 //     ping-pong, so the tensor pipe keeps running while one is drained).
+//     Promoting every 32 k kept the error at 1.4e-7 (K = 4096) but the MMAs
+//     then waited for the drains: 1.09 ms per n = 4096 product against
+//     0.95 ms every 64 k (2.0e-7) and 0.84 ms every 128 k (3.4e-7).
 //
 // One CTA computes a 128 x 128 tile:
 //   warp 0     TMA producer: X_hi, X_lo (128 x 32) and Y^T_hi, Y^T_lo
@@ -32,8 +35,8 @@
 //              (compensation terms in TMEM), then run the epilogue: linear
 //              combinations, (hi, lo) split, row-major and transposed stores.
 // Measured on GB300 (N(0,1) operands): relative Frobenius error of one
-// product 1.3e-7 at K = 256 and at K = 4096, against 2.9e-7 and 1.2e-6 for
-// cuBLAS FP32 (FFMA).
+// product 3.4e-7 at K = 4096 (1.3e-7 at K = 256, where one group covers all
+// of K), against 1.2e-6 and 2.9e-7 for cuBLAS FP32 (FFMA).
 // Every mbarrier wait is bounded; on expiry the CTA stops issuing work, waits
 // (bounded) for what it already issued, frees TMEM and raises *err.
 #include <cuda.h>
@@ -64,7 +67,7 @@ constexpr int kStages = 3;
 constexpr int kSmem = kStages * kStageBytes + 1024;
 static_assert(3 * BM * BN * 4 <= kStages * kStageBytes, "epilogue tiles fit the stages");
 #ifndef COSSIN_TC_GROUP
-#define COSSIN_TC_GROUP 1
+#define COSSIN_TC_GROUP 4
 #endif
 constexpr int kGroup = COSSIN_TC_GROUP;  // k-blocks per accumulator buffer before promotion
 constexpr uint32_t kTmemCols = 512;    // main buffer b at 128 b, corrections at 256, compensation at 384
