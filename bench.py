@@ -456,19 +456,20 @@ def forms(api, wsp):
         torch.cuda.empty_cache()
     return {"n": [N, 2 * N], "family": "normal", "precisions": out, "fp64_emu_product": emu_product_form(api),
             "bf16x4_product": emu_product_form(api, prec="split_bf16"),
+            "tf32x4_product": emu_product_form(api, prec="split_tf32"),
             "batched": batched_form(api), "adjoint": adjoint_form(api), "cs": cs_form(api, wsp)}
 
 
 def emu_product_form(api, reps=5, prec="fp64_emu"):
-    """One n = 4096 product on the BF16 tensor cores from 7-bit slices: eight
-    slices (prec "fp64_emu", 36 slice products, FP64-class) or four (prec
-    "split_bf16", 10 slice products, FP32-class).  The kernel's time from its
-    own CUDA events, the slice products it issues against the measured BF16
-    peak, the FP64 rate it stands for, and its difference to the native FP64
-    product."""
+    """One n = 4096 tensor-core product: on the BF16 tensor cores from 7-bit
+    slices, eight (prec "fp64_emu", 36 slice products, FP64-class) or four
+    (prec "split_bf16", 10 slice products, FP32-class), or the four-pass TF32
+    product of (hi, lo) splits (prec "split_tf32").  The kernel's time from
+    its own CUDA events, the work it issues against the tensor peak, the FP64
+    rate it stands for, and its difference to the native FP64 product."""
     import torch
     from paper_2010_00465_gb300 import inputs
-    pairs = 36 if prec == "fp64_emu" else 10
+    pairs = {"fp64_emu": 36, "split_bf16": 10, "split_tf32": 4}[prec]
     X = torch.from_numpy(inputs.matrix(N, "normal", None, index=1)).cuda()
     Y = torch.from_numpy(inputs.matrix(N, "normal", None, index=5)).cuda()
     P = api.matmul(X, Y, prec)
@@ -484,18 +485,26 @@ def emu_product_form(api, reps=5, prec="fp64_emu"):
     torch.cuda.synchronize()
     call_ms = (time.perf_counter() - t0) * 1e3 / reps
     api.prof_enable(False)
-    ms, launches, work = api.prof_read("gemm_emu")
+    tf32 = prec == "split_tf32"
+    ms, launches, work = api.prof_read("gemm_tf32" if tf32 else "gemm_emu")
     kms = ms / max(launches, 1)
     pk, pk_kind = peaks()
     issued = pairs * 2.0 * N ** 3 / (kms / 1e3) / 1e12
     native = 2.0 * N ** 3
-    key = "ozaki_kernel" if pairs == 36 else "ozaki_kernel_s4"
+    key = {"fp64_emu": "ozaki_kernel", "split_bf16": "ozaki_kernel_s4", "split_tf32": "gemm_tf32_kernel"}[prec]
+    if tf32:
+        # TF32 has no measured peak here: the BF16 burst scaled by the nominal
+        # dense ratio 1.1 / 2.25 PFLOP/s
+        peak = pk["bf16_tflops"] * 1.1 / 2.25
+        note = ("4 TF32 passes per product (hi*hi, lo*hi, hi*lo, lo*lo); peak = cuBLAS BF16 burst x 1.1/2.25 "
+                "(nominal TF32/BF16 dense ratio), " + pk_kind)
+    else:
+        peak = pk["bf16_tflops"]
+        note = "%d BF16 slice products per product; peak = cuBLAS BF16 burst, " % pairs + pk_kind
     return {"n": N, "prec": prec, "kernel_ms": kms, "call_ms_with_slicing_and_alloc": call_ms,
             "fp64_equivalent_tflops": native / (kms / 1e3) / 1e12, "rel_diff_vs_fp64_product": rel,
-            "roofline": {"bound": "tensor", "achieved": issued, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                         "frac": issued / pk["bf16_tflops"], "traffic": traffic_of(key),
-                         "note": "%d BF16 slice products per product; " % pairs +
-                         "peak = cuBLAS BF16 burst, " + pk_kind}}
+            "roofline": {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
+                         "frac": issued / peak, "traffic": traffic_of(key), "note": note}}
 
 
 def cs_form(api, wsp):
@@ -638,7 +647,23 @@ def batched_form(api, count=20000, reps=5):
             "sample": "2 largest orders, 3 largest norms, 6 random",
             "fp64_plain_path_ms": 1e3 * t64,
             "fp64_plain_path_method": "all %d matrices through cossin(fp64), one call each, wall clock" % count,
-            "speedup_vs_fp64_plain_path": 1e3 * t64 / ms}
+            "speedup_vs_fp64_plain_path": 1e3 * t64 / ms,
+            "roofline": batched_roofline(flops, ms)}
+
+
+def batched_roofline(flops, ms):
+    """The batched kernel against the tensor pipe it issues its products to:
+    every product is ten BF16 slice products (four slices per operand, p + q
+    <= 3), so the issued work is 10x the algorithmic; the peak is the measured
+    sustained BF16 rate.  The kernel is bound by the CUDA-core work around the
+    products (slicing, double-float epilogues), which this fraction shows."""
+    pk, pk_kind = peaks()
+    issued = 10.0 * flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": issued, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+            "frac": issued / pk["bf16_tflops_sustained"], "traffic": traffic_of("batched_kernel"),
+            "kernel": "batched_kernel<128, 512>",
+            "note": "10 BF16 slice products per product; peak = sustained bf16, " + pk_kind +
+                    "; bound in practice by CUDA-core issue (slicing, double-float epilogues)"}
 
 
 def ncu_case(name):
