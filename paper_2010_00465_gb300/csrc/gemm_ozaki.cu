@@ -135,27 +135,29 @@ constexpr uint32_t kIdesc2 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 constexpr uint32_t kIdesc4 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((4 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-// The slice products of A slice p: B slices q = 0 .. S - 1 - p in groups of
-// 4, 2 and 1 adjacent slices (group grp starts at group_start, spans
-// group_width, 0 past the last), one instruction each; a wider instruction
+// The slice products of A slice p with the B slices q in [qb, qe), in runs
+// of 4, 2 and 1 adjacent slices (run grp starts at run_start, spans
+// run_width, 0 past the last), one instruction each; a wider instruction
 // reads the A operand from shared memory once for more slice pairs.
-__host__ __device__ constexpr int group_width(int S, int p, int grp) {
-  int q = 0, w = 0;
-  for (int i = 0; i <= grp; ++i) {
-    q += w;
-    const int left = S - p - q;
-    w = left >= 4 ? 4 : left >= 2 ? 2 : left >= 1 ? 1 : 0;
-  }
-  return w;
-}
-__host__ __device__ constexpr int group_start(int S, int p, int grp) {
-  int q = 0;
-  for (int i = 0; i < grp; ++i) q += group_width(S, p, i);
+__host__ __device__ constexpr int run_of(int left) { return left >= 4 ? 4 : left >= 2 ? 2 : left >= 1 ? 1 : 0; }
+__host__ __device__ constexpr int run_start(int qb, int qe, int grp) {
+  int q = qb;
+  for (int i = 0; i < grp; ++i) q += run_of(qe - q);
   return q;
 }
-static_assert(group_width(8, 1, 0) == 4 && group_width(8, 1, 1) == 2 && group_width(8, 1, 2) == 1 &&
-                  group_start(8, 1, 2) == 6 && group_width(8, 0, 2) == 0 && group_width(4, 3, 0) == 1,
-              "slice groups");
+__host__ __device__ constexpr int run_width(int qb, int qe, int grp) { return run_of(qe - run_start(qb, qe, grp)); }
+// The B slices of A slice p in phase ph: all of them with one phase, else the
+// levels p + q below S / 2 (ph = 0) or from S / 2 on (ph = 1).
+__host__ __device__ constexpr int phase_q_begin(int S, int phases, int ph, int p) {
+  return phases == 1 || ph == 0 ? 0 : (S / 2 - p > 0 ? S / 2 - p : 0);
+}
+__host__ __device__ constexpr int phase_q_end(int S, int phases, int ph, int p) {
+  return phases == 1 || ph == 1 ? S - p : (S / 2 - p > 0 ? S / 2 - p : 0);
+}
+static_assert(run_width(0, 7, 0) == 4 && run_width(0, 7, 1) == 2 && run_width(0, 7, 2) == 1 &&
+                  run_start(0, 7, 2) == 6 && run_width(0, 8, 2) == 0 && run_width(3, 7, 0) == 4 &&
+                  phase_q_begin(8, 2, 1, 1) == 3 && phase_q_end(8, 2, 0, 1) == 3 && phase_q_end(8, 2, 0, 5) == 0,
+              "slice runs");
 
 // Shared-memory descriptors (built in the MMA loop): K-major, 64-byte
 // swizzle, rows of 64 bytes, 8-row (512-byte) atoms stacked along M/N
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // (S = 4): the MMAs of chunk c + 1 run while the epilogue drains chunk c.
   constexpr int kBufs = 2 * S * BN <= 512 ? 2 : 1;
   constexpr uint32_t kTmemCols = (uint32_t)(S * BN * kBufs);
+  constexpr int kPhases = kBufs == 1 ? 2 : 1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kStages];
@@ -479,41 +482,52 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool wait_free = kk == 0 && cg >= kBufs;
             const uint32_t free_par = (uint32_t)((cg / kBufs - 1) & 1);
             bool stop = false;
+            // With one set of accumulators (S = 8) a stage's MMAs run in two
+            // phases, levels below S / 2 for every k-step, then the rest: at
+            // a chunk start the first phase needs only the lower levels back
+            // from the draining warps, which free them first.
 #pragma unroll
-            for (int j = 0; j < BK / 16 && !stop; ++j) {  // K = 16 bf16 (32 bytes) per instruction
+            for (int ph = 0; ph < kPhases; ++ph) {
 #pragma unroll
-              for (int p = 0; p < S; ++p) {
-                const uint64_t ad =
-                    ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
-                // B slices q .. q + w - 1 in one N = w BN instruction into
-                // the accumulators of levels p + q .. p + q + w - 1 < S
+              for (int j = 0; j < BK / 16; ++j) {  // K = 16 bf16 (32 bytes) per instruction
 #pragma unroll
-                for (int grp = 0; grp < 3; ++grp) {
-                  const int w = group_width(S, p, grp);
-                  if (w == 0) break;
-                  const int q = group_start(S, p, grp);
-                  const uint64_t bd =
-                      ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
-                  // p = 0 touches every level first: there a chunk restarts
-                  // its accumulators, after the epilogue has read them
-                  const bool restart = chunk_start && j == 0 && p == 0;
-                  if (restart && wait_free) {
-                    bool freed = true;
+                for (int p = 0; p < S; ++p) {
+                  const int qb = phase_q_begin(S, kPhases, ph, p), qe = phase_q_end(S, kPhases, ph, p);
+                  if (qb >= qe) continue;
+                  const uint64_t ad =
+                      ((uint64_t)kDescHi << 32) | (uint64_t)(a_lo + (uint32_t)((p * kABytes + 32 * j) >> 4));
+                  // B slices q .. q + w - 1 in one N = w BN instruction into
+                  // the accumulators of levels p + q .. p + q + w - 1 < S
 #pragma unroll
-                    for (int l = 0; l < 4; ++l)
-                      if (l < w) freed = freed && mbar_wait(&free_bar[buf][q + l], free_par, &abort_flag);
-                    if (!freed) {
-                      abort_flag = 1;
-                      stop = true;
-                      break;
+                  for (int grp = 0; grp < 3; ++grp) {
+                    const int w = run_width(qb, qe, grp);
+                    if (w == 0) break;
+                    const int q = run_start(qb, qe, grp);
+                    const uint64_t bd =
+                        ((uint64_t)kDescHi << 32) | (uint64_t)(b_lo + (uint32_t)((q * kBBytes + 32 * j) >> 4));
+                    // p = 0 touches each level of a phase first: there a chunk
+                    // restarts its accumulators, after the epilogue has read them
+                    const bool restart = chunk_start && j == 0 && p == 0;
+                    if (restart && wait_free) {
+                      bool freed = true;
+#pragma unroll
+                      for (int l = 0; l < 4; ++l)
+                        if (l < w) freed = freed && mbar_wait(&free_bar[buf][q + l], free_par, &abort_flag);
+                      if (!freed) {
+                        abort_flag = 1;
+                        stop = true;
+                        break;
+                      }
+                      tc_fence_after();
                     }
-                    tc_fence_after();
+                    mma_bf16(acc0 + (uint32_t)((p + q) * BN), ad, bd, w == 4 ? kIdesc4 : w == 2 ? kIdesc2 : kIdesc1,
+                             restart ? 0u : 1u);
                   }
-                  mma_bf16(acc0 + (uint32_t)((p + q) * BN), ad, bd, w == 4 ? kIdesc4 : w == 2 ? kIdesc2 : kIdesc1,
-                           restart ? 0u : 1u);
+                  if (stop) break;
                 }
                 if (stop) break;
               }
+              if (stop) break;
             }
             if (stop) break;
             mma_commit(&empty_bar[st]);
