@@ -708,14 +708,21 @@ def ncu_case(name):
     return 0
 
 
-def launches_of(prec, info):
-    """Kernels one cossin call launches: the 1-norm (2); FP64: one kernel per
-    product; FP32: the input conversion, per product the emulated product's
+def launches_of(prec, info, n=None):
+    """Kernels one cossin call launches: the 1-norm (2); then Pi_2m chain
+    products and s double-angle products (one stacked 2n x n x n product each;
+    info["products"] counts those twice).  FP64: one or two kernels per
+    product (two when the last wave of tiles is split over K, as the library
+    reports); FP32: the input conversion, per product the emulated product's
     five slicing kernels, a memset and the product kernel, and the two output
     conversions."""
+    s = info["s"]
+    chain = info["products"] - 2 * s
     if prec == "fp64":
-        return 2 + info["products"]
-    return 2 + 1 + 7 * info["products"] + 2
+        from paper_2010_00465_gb300 import api
+        n = n or N
+        return 2 + chain * api.fp64_product_launches(n, n, n) + s * api.fp64_product_launches(2 * n, n, n)
+    return 2 + 1 + 7 * (chain + s) + 2
 
 
 def traffic_of(kernel):

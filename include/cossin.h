@@ -217,6 +217,13 @@ cs_status cossin_selftest_wait_timeout(cossin_stream_t stream);
  * allocates a small stream-ordered scratch. */
 cs_status cossin_fp64_fma_rate(int64_t rounds, double* tflops, cossin_stream_t stream);
 
+/* Kernels one FP64 product of an M x N result with inner dimension K
+ * launches inside cossin / cossin_ex on the current device (the paper has no
+ * counterpart): 2 when the tiles of its last, partial wave are split over K
+ * (a second kernel adds the pieces and runs the epilogue), else 1; 0 for an
+ * empty product.  For launch accounting; queues no work. */
+cs_status cossin_fp64_product_launches(int64_t M, int64_t N, int64_t K, int32_t* launches);
+
 /* Allocation-failure self test (the paper has no counterpart): the next
  * `count` device allocations the library makes for itself (the workspaces of
  * cossin, cossin_cs, cossin_unitary without ws, cossin_norm1, cossin_matmul

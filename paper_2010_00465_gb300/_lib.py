@@ -67,6 +67,7 @@ SIGNATURES = {
     "cossin_selftest_wait_timeout": (ctypes.c_int, [_vp]),
     "cossin_selftest_fail_next_alloc": (None, [_i32]),
     "cossin_fp64_fma_rate": (ctypes.c_int, [_i64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "cossin_fp64_product_launches": (ctypes.c_int, [_i64, _i64, _i64, ctypes.POINTER(ctypes.c_int32)]),
     "cossin_backward_workspace_size": (ctypes.c_int, [_i64, _i64, ctypes.c_int, _i32, ctypes.POINTER(_sz)]),
     "cossin_backward_ws": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int, _vp, _sz,
                                           _vp, _vp]),

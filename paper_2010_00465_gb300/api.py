@@ -293,6 +293,15 @@ def fp64_fma_rate(rounds: int = 16384, stream=None) -> float:
     return float(out.value)
 
 
+def fp64_product_launches(M: int, N: int, K: int) -> int:
+    """Kernels one FP64 product (M x N result, inner K) launches inside cossin
+    on the current device: 2 when its last partial wave of tiles is split
+    over K, else 1."""
+    out = ctypes.c_int32()
+    check(lib().cossin_fp64_product_launches(int(M), int(N), int(K), ctypes.byref(out)))
+    return int(out.value)
+
+
 def selftest_fail_next_alloc(count: int = 1) -> None:
     """Test hook: the library's next ``count`` device allocations fail (CS_ENOMEM)."""
     lib().cossin_selftest_fail_next_alloc(int(count))

@@ -160,6 +160,11 @@ Layout make_layout(int64_t n, int prec, bool with_outputs) {
     for (int k = 0; k < 4; ++k) L.c4[k] = take(sz);
     L.p32 = take(sz);
   }
+  if (!uses_emu((cs_prec)prec)) {
+    // native FP64 products: the pieces of the tiles split over K
+    L.splitk_bytes = std::max(gemm_f64_split_bytes(n, n, n), gemm_f64_split_bytes(2 * n, n, n));
+    if (L.splitk_bytes) L.splitk = take(L.splitk_bytes);
+  }
   if (uses_emu((cs_prec)prec)) {
     // the stacked double-angle product is the largest emulated one
     L.ozaki_bytes = ozaki_dims(2 * n, n, n, 1, square_slices((cs_prec)prec)).total;
@@ -396,16 +401,12 @@ cs_status run_plan_f64(const void* A, int64_t n, cs_prec prec, void* C, void* S,
   return convert_f64_f32(fin + n2, (float*)S, n2, stream);
 }
 
-namespace {
-
-}  // namespace
-
 // Double-angle steps (Sec. 1): [C'; S'] = [C; S] C with C' = 2X - I, S' = 2X,
 // one stacked 2n x n x n product per step, ping-ponging between the buffers.
 cs_status F64Product::operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
                                  const Epilogue<double>& e, cudaStream_t stream) const {
   if (emu_work) return gemm_f64_emu(X, Y, M, N, K, K, N, e, N, emu_work, emu_bytes, err, stream, slices);
-  return gemm_f64(X, Y, M, N, K, K, N, false, false, e, N, 1, 0, 0, 0, stream);
+  return gemm_f64(X, Y, M, N, K, K, N, false, false, e, N, 1, 0, 0, 0, stream, split_work, split_bytes);
 }
 
 int square_slices(cs_prec prec) { return prec == CS_FP32 ? kOzakiSlicesSplit : kOzakiSlices; }
@@ -417,6 +418,9 @@ F64Product f64_product(cs_prec prec, char* ws, const Layout& L) {
     p.emu_bytes = L.ozaki_bytes;
     p.err = tc_error_word();
     p.slices = square_slices(prec);
+  } else if (L.splitk_bytes) {
+    p.split_work = ws + L.splitk;
+    p.split_bytes = L.splitk_bytes;
   }
   return p;
 }
@@ -496,10 +500,6 @@ cs_status read_norm(const double* dev, double* host, cudaStream_t stream) {
   }
   return CS_OK;
 }
-
-namespace {
-
-}  // namespace
 
 cs_status run_tf32(const double* A, int64_t n, cs_prec prec, double* C, double* S, char* ws, const Layout& L,
                    const PlanSpec& P, cudaStream_t stream);

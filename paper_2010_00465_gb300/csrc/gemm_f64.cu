@@ -52,20 +52,50 @@ __device__ __forceinline__ void epilogue_store(const Epilogue<double>& epi, int6
   }
 }
 
+// Split of the last, partial wave of tiles over K (one product, batch 1):
+// the grid is one-dimensional over the tiles in row-major order; tiles from
+// `first` on are cut into `parts` k-ranges of `kchunk`, whose partial sums go
+// to ws (one TILE x TILE block per piece, in each thread's register order)
+// and are added, in piece order, by gemm_f64_split_finish, which then runs
+// the epilogue.  parts == 0: the plain three-dimensional grid.
+struct SplitK {
+  int64_t first = 0;
+  int64_t kchunk = 0;
+  int parts = 0;
+  int ntn = 0;  // tile columns
+  double* ws = nullptr;
+};
+
 // TILE x TILE block tile (TILE = 128 or 64); thread (ty, tx) of 16 x 16 owns
 // rows {h*64 + ty*4 + i} and columns {h*64 + tx*4 + j}, h < TILE/64, i, j < 4.
 template <int TILE, bool TX, bool TY>
 __global__ void __launch_bounds__(THREADS)
 gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int64_t M, int64_t N,
                 int64_t K, int64_t ldx, int64_t ldy, int64_t ldo, int64_t bsx, int64_t bsy,
-                int64_t bse, const Epilogue<double> epi) {
+                int64_t bse, const Epilogue<double> epi, const SplitK sk) {
   constexpr int BM = TILE, BN = TILE, R = TILE / 16;
   __shared__ double Xs[BK][BM];
   __shared__ double Ys[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  const int64_t b = blockIdx.z;
+  int64_t m0, n0, b = 0, kbeg = 0, kend = K;
+  double* part = nullptr;  // this piece's partial sums (split tiles only)
+  if (sk.parts == 0) {
+    m0 = (int64_t)blockIdx.y * BM;
+    n0 = (int64_t)blockIdx.x * BN;
+    b = blockIdx.z;
+  } else {
+    int64_t t = blockIdx.x;
+    if (t >= sk.first) {
+      const int64_t piece = t - sk.first;
+      t = sk.first + piece / sk.parts;
+      kbeg = (piece % sk.parts) * sk.kchunk;
+      kend = min(K, kbeg + sk.kchunk);
+      part = sk.ws + piece * (int64_t)(BM * BN);
+    }
+    m0 = (t / sk.ntn) * BM;
+    n0 = (t % sk.ntn) * BN;
+  }
   X += b * bsx;
   Y += b * bsy;
 
@@ -75,7 +105,7 @@ gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int6
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
 
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     // op(X) tile: rows m0..m0+127, columns k0..k0+7, stored k-major.
 #pragma unroll
     for (int t = 0; t < (BM * BK) / THREADS; ++t) {
@@ -127,6 +157,14 @@ gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int6
     __syncthreads();
   }
 
+  if (part) {  // a piece of a split tile: its partial sums, for the finishing kernel
+    double2* dst = reinterpret_cast<double2*>(part + (int64_t)tid * R * R);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; j += 2) dst[(i * R + j) / 2] = make_double2(acc[i][j], acc[i][j + 1]);
+    return;
+  }
   // Epilogue over this thread's rows and columns of the block tile.
   const int64_t eoff = b * bse;
 #pragma unroll
@@ -138,6 +176,42 @@ gemm_f64_kernel(const double* __restrict__ X, const double* __restrict__ Y, int6
       const int64_t c = n0 + (j / 4) * 64 + tx * 4 + (j % 4);
       if (c >= N) continue;
       epilogue_store(epi, eoff, r, c, ldo, acc[i][j]);
+    }
+  }
+}
+
+// The split tiles: tile first + blockIdx.x adds its pieces' partial sums in
+// piece order and runs the epilogue, with the main kernel's thread layout.
+template <int TILE>
+__global__ void __launch_bounds__(THREADS)
+gemm_f64_split_finish(int64_t M, int64_t N, int64_t ldo, const Epilogue<double> epi, const SplitK sk) {
+  constexpr int R = TILE / 16;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t t = sk.first + blockIdx.x;
+  const int64_t m0 = (t / sk.ntn) * TILE, n0 = (t % sk.ntn) * TILE;
+  const double* base = sk.ws + (int64_t)blockIdx.x * sk.parts * (TILE * TILE) + (int64_t)tid * R * R;
+  double acc[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = base[i * R + j];
+  for (int p = 1; p < sk.parts; ++p) {
+    const double* src = base + (int64_t)p * (TILE * TILE);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[i][j] += src[i * R + j];
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int64_t r = m0 + (i / 4) * 64 + ty * 4 + (i % 4);
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int64_t c = n0 + (j / 4) * 64 + tx * 4 + (j % 4);
+      if (c >= N) continue;
+      epilogue_store(epi, 0, r, c, ldo, acc[i][j]);
     }
   }
 }
@@ -175,11 +249,70 @@ gemm_f64_small_kernel(const double* __restrict__ X, const double* __restrict__ Y
   if (r < M && c < N) epilogue_store(epi, b * bse, r, c, ldo, acc);
 }
 
+// How to split the last wave of 128-wide tiles of one M x N x K product
+// over K: the tiles that do not fill a last wave of the SMs' resident CTAs
+// (W per wave) run as `parts` pieces each, so that the pieces spread over all
+// the SMs (a partial wave of tail tiles takes a whole tile time; tail x parts
+// pieces take ceil(tail parts / W) / parts of one).  parts = 0: no split.
+struct SplitPlan {
+  int64_t tiles = 0, tail = 0, kchunk = 0;
+  int parts = 0, ntn = 0;
+  size_t bytes = 0;
+};
+
+int resident_ctas_128(int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_f64_kernel<128, false, false>, THREADS, 0) !=
+          cudaSuccess ||
+      per_sm <= 0)
+    per_sm = 1;
+  return sms * per_sm;
+}
+
+SplitPlan split_plan(int64_t M, int64_t N, int64_t K, int sms) {
+  SplitPlan sp;
+  const int64_t ntm = (M + 127) / 128;
+  sp.ntn = (int)((N + 127) / 128);
+  sp.tiles = ntm * sp.ntn;
+  if (sms <= 0 || sp.tiles < 2 * (int64_t)sms) return sp;  // the 128-wide kernel runs from two waves on
+  const int64_t W = resident_ctas_128(sms);
+  sp.tail = sp.tiles % W;
+  if (sp.tail == 0) return sp;
+  double best = 1.0;
+  int parts = 1;
+  for (int q = 2; q <= 4; ++q) {
+    if (K / q < 512) break;  // pieces of at least 512 k
+    const double cost = (double)((sp.tail * q + W - 1) / W) / q;
+    if (cost < best - 0.05) {
+      best = cost;
+      parts = q;
+    }
+  }
+  if (parts == 1) return sp;
+  sp.kchunk = ((K + parts - 1) / parts + BK - 1) / BK * BK;
+  sp.parts = (int)((K + sp.kchunk - 1) / sp.kchunk);
+  sp.bytes = (size_t)sp.tail * sp.parts * 128 * 128 * sizeof(double);
+  return sp;
+}
+
+int current_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
+}
+
 }  // namespace
+
+size_t gemm_f64_split_bytes(int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0) return 0;
+  return split_plan(M, N, K, current_sms()).bytes;
+}
 
 cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64_t K, int64_t ldx,
                    int64_t ldy, bool transX, bool transY, const Epilogue<double>& epi, int64_t ldo,
-                   int64_t batch, int64_t bsx, int64_t bsy, int64_t bse, cudaStream_t stream) {
+                   int64_t batch, int64_t bsx, int64_t bsy, int64_t bse, cudaStream_t stream, void* split_ws,
+                   size_t split_bytes) {
   if (M <= 0 || N <= 0 || batch <= 0) return CS_OK;
   // 128-wide tiles unless that leaves fewer than two waves of CTAs (small
   // batched products), where 64-wide tiles balance the SMs better.
@@ -213,21 +346,39 @@ cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64
     CS_CUDA_CHECK(cudaGetLastError());
     return CS_OK;
   }
+  SplitK sk;
+  if (tile == 128 && batch == 1 && split_ws) {
+    const SplitPlan sp = split_plan(M, N, K, sms);
+    if (sp.parts > 1 && sp.bytes <= split_bytes) {
+      sk.first = sp.tiles - sp.tail;
+      sk.kchunk = sp.kchunk;
+      sk.parts = sp.parts;
+      sk.ntn = sp.ntn;
+      sk.ws = (double*)split_ws;
+      const int64_t ctas = sk.first + sp.tail * sp.parts;
+      if (ctas > INT32_MAX) return fail(CS_EINVAL, "gemm_f64: grid too large");
+      grid = dim3((unsigned)ctas, 1, 1);
+    }
+  }
 #define CS_F64_LAUNCH(T)                                                                                           \
   if (!transX && !transY)                                                                                          \
-    gemm_f64_kernel<T, false, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi); \
+    gemm_f64_kernel<T, false, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi, sk); \
   else if (transX && !transY)                                                                                      \
-    gemm_f64_kernel<T, true, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);  \
+    gemm_f64_kernel<T, true, false><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi, sk);  \
   else if (!transX && transY)                                                                                      \
-    gemm_f64_kernel<T, false, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);  \
+    gemm_f64_kernel<T, false, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi, sk);  \
   else                                                                                                             \
-    gemm_f64_kernel<T, true, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi);
+    gemm_f64_kernel<T, true, true><<<grid, THREADS, 0, stream>>>(X, Y, M, N, K, ldx, ldy, ldo, bsx, bsy, bse, epi, sk);
   if (tile == 64) {
     CS_F64_LAUNCH(64)
   } else {
     CS_F64_LAUNCH(128)
   }
 #undef CS_F64_LAUNCH
+  if (sk.parts > 1) {
+    CS_CUDA_CHECK(cudaGetLastError());
+    gemm_f64_split_finish<128><<<(unsigned)(grid.x - sk.first) / (unsigned)sk.parts, THREADS, 0, stream>>>(M, N, ldo, epi, sk);
+  }
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }
@@ -256,6 +407,13 @@ __global__ void fma_rate_kernel(double* out, long long rounds, double b, double 
 }  // namespace
 
 }  // namespace cs
+
+extern "C" cs_status cossin_fp64_product_launches(int64_t M, int64_t N, int64_t K, int32_t* launches) {
+  using namespace cs;
+  if (!launches || M < 0 || N < 0 || K < 0) return fail(CS_EINVAL, "cossin_fp64_product_launches: bad arguments");
+  *launches = (M == 0 || N == 0) ? 0 : (gemm_f64_split_bytes(M, N, K) > 0 ? 2 : 1);
+  return CS_OK;
+}
 
 extern "C" cs_status cossin_fp64_fma_rate(int64_t rounds, double* tflops, cossin_stream_t stream) {
   using namespace cs;

@@ -115,7 +115,11 @@ struct ProfScope {
 cs_status gemm_f64(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
                    int64_t ldx, int64_t ldy, bool transX, bool transY, const Epilogue<double>& epi,
                    int64_t ldo, int64_t batch, int64_t bsx, int64_t bsy, int64_t bse,
-                   cudaStream_t stream);
+                   cudaStream_t stream, void* split_ws = nullptr, size_t split_bytes = 0);
+// Scratch that lets gemm_f64 split the tiles of its last, partial wave over K
+// (one product, batch 1; 0 when it would not split); given at least this
+// many bytes, gemm_f64 does.
+size_t gemm_f64_split_bytes(int64_t M, int64_t N, int64_t K);
 
 // ||A||_1 for an FP64 or FP32 matrix into a device double (*out_dev).
 // partial_dev: scratch of norm1_scratch_elems(n) doubles (column partial sums,

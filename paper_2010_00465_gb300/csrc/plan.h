@@ -70,6 +70,7 @@ struct Layout {
   size_t c4[4] = {};
   size_t p32 = 0;
   size_t ozaki = 0, ozaki_bytes = 0;  // scratch of one emulated product
+  size_t splitk = 0, splitk_bytes = 0;  // native FP64 products: last-wave pieces split over K
   size_t out_c = 0, out_s = 0;  // n x n C and S of the precision's type (with_outputs)
   size_t total = 0;
 };
@@ -82,6 +83,8 @@ Layout make_layout(int64_t n, int prec, bool with_outputs = false);
 struct F64Product {
   void* emu_work = nullptr;
   size_t emu_bytes = 0;
+  void* split_work = nullptr;  // native FP64: scratch for splitting the last wave over K
+  size_t split_bytes = 0;
   int* err = nullptr;
   int slices = kOzakiSlices;
   cs_status operator()(const double* X, const double* Y, int64_t M, int64_t N, int64_t K,
