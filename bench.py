@@ -693,8 +693,10 @@ def ncu_case(name):
         torch.cuda.synchronize()
         plan.close()
     elif name == "gemm_f64":
-        X = torch.from_numpy(inputs.matrix(N, "normal", 1.0, index=1)).cuda()
-        api.matmul(X, X, "fp64")
+        # the headline FP64 matrix at ||A||_1 = 2^-4: (2m, s) = (8, 0), four
+        # products through the cos/sin workspace (last wave split over K)
+        A = torch.from_numpy(inputs.matrix(N, "normal", 2.0 ** -4, index=1)).cuda()
+        api.cossin(A, "fp64")
     elif name == "gemm_emu":
         # one n = 4096 FP64 product emulated on the BF16 tensor cores (eight
         # slices), then one four-slice product
