@@ -241,7 +241,8 @@ void cossin_selftest_fail_next_alloc(int32_t count);
  * operands taken to FP64 and the product rounded to FP32 once; n <= 8192
  * for these three).  These are the products the method counts (Pi_2m
  * in Tables 1-2).  P must not overlap X or Y.  Allocates and frees a
- * stream-ordered workspace for the tensor-core kinds. */
+ * stream-ordered workspace for the tensor-core kinds, and for CS_FP64 when
+ * the product's last wave of tiles is split over K (as inside cossin). */
 cs_status cossin_matmul(const void* X_dev, const void* Y_dev, int64_t n, cs_prec prec, void* P_dev,
                         cossin_stream_t stream);
 

@@ -690,7 +690,13 @@ cs_status cossin_matmul(const void* X, const void* Y, int64_t n, cs_prec prec, v
   e.alpha[0] = 1.0;
   if (prec == CS_FP64) {
     e.out[0] = (double*)P;
-    return cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st);
+    const size_t split = cs::gemm_f64_split_bytes(n, n, n);
+    void* sw = nullptr;
+    if (split) CS_CHECK(cs::dev_alloc(&sw, split, st, "cossin_matmul split scratch"));
+    const cs_status rc =
+        cs::gemm_f64((const double*)X, (const double*)Y, n, n, n, n, n, false, false, e, n, 1, 0, 0, 0, st, sw, split);
+    if (sw) cudaFreeAsync(sw, st);
+    return rc;
   }
   // Emulated products; CS_FP32 takes FP32 operands to FP64 and rounds the
   // product to FP32 once.

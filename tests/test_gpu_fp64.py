@@ -6,6 +6,8 @@ oracle is too slow for a dense matrix, so the comparison uses a permuted
 block-diagonal matrix, whose cos and sin the oracle computes block by block,
 and properties that hold at any size for a dense one.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -265,3 +267,31 @@ def test_host_tensors_round_trip(pinned):
     assert torch.equal(C2, C) and torch.equal(S2, S)
     with pytest.raises(ValueError):
         api.cossin(host_A, "fp64", out=(torch.empty(3, 3, dtype=torch.float64), out[1]))
+
+
+@pytest.mark.parametrize("n", [2304, 2500, 4096, 4100])
+def test_product_with_split_last_wave(n):
+    """The FP64 product whose last, partial wave of tiles runs as pieces split
+    over K (2, 3 or 4 pieces at these orders on a 152-SM GB300, K a multiple
+    of the piece length or not): sampled entries, most in the split tiles at
+    the bottom of the matrix, against exactly summed dot products, within the
+    K u bound of an FP64 product."""
+    X = inputs.matrix(n, "normal", None, index=61, sub=n)
+    Y = inputs.matrix(n, "normal", None, index=62, sub=n)
+    P = api.matmul(dev(X), dev(Y), "fp64").cpu().numpy()
+    g = inputs.rng(61, n)
+    rows = np.concatenate([g.integers(0, n, 8), n - 1 - g.integers(0, min(n, 384), 24)])
+    cols = g.integers(0, n, rows.size)
+    for r, c in zip(rows, cols):
+        terms = X[r, :] * Y[:, c]
+        ref = math.fsum(terms.tolist())
+        scale = math.fsum(np.abs(terms).tolist())
+        assert abs(P[r, c] - ref) <= n * 2.0 ** -53 * scale, (r, c)
+    assert api.fp64_product_launches(n, n, n) in (1, 2)
+
+
+def test_product_launch_query():
+    assert api.fp64_product_launches(64, 64, 64) == 1
+    assert api.fp64_product_launches(0, 64, 64) == 0
+    with pytest.raises(_lib.CossinError):
+        api.fp64_product_launches(-1, 64, 64)
