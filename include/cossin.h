@@ -110,7 +110,8 @@ typedef struct {
 } cs_info;
 
 /* Bytes of device workspace cossin_ex needs for one n x n matrix in `prec`.
- * Host-only; never touches the GPU. */
+ * Host-only: queues no work and creates no context; it reads the current
+ * device's SM count (the FP64 and emulated products keep per-SM scratch). */
 cs_status cossin_workspace_size(int64_t n, cs_prec prec, size_t* bytes);
 
 /* Steps 1-2 only.  theta = ||A||_1 of the device matrix A_dev (FP32 for

@@ -260,14 +260,10 @@ struct SplitPlan {
   size_t bytes = 0;
 };
 
-int resident_ctas_128(int sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_f64_kernel<128, false, false>, THREADS, 0) !=
-          cudaSuccess ||
-      per_sm <= 0)
-    per_sm = 1;
-  return sms * per_sm;
-}
+// One 128-wide CTA per SM: 256 threads of about 200 registers each (the
+// plan only needs the count to balance the pieces, not to be correct, and the
+// workspace query that sizes their scratch must not create a context).
+int resident_ctas_128(int sms) { return sms; }
 
 SplitPlan split_plan(int64_t M, int64_t N, int64_t K, int sms) {
   SplitPlan sp;
