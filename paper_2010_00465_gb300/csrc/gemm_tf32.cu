@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int g = 0; g < num_groups; ++g) {
       const int b = g & 1;
-      // lane 0 waits and the warp follows its verdict, so the warp-collective
+      // lane 0 waits and the warp follows its outcome, so the warp-collective
       // TMEM loads below are never reached by part of a warp
       int w = 1;
       if (lane == 0) {
