@@ -261,8 +261,10 @@ __global__ void __launch_bounds__(256) col_max_kernel(const double* __restrict__
 
 __global__ void col_exp_kernel(const double* __restrict__ Y, int64_t ld, const unsigned long long* __restrict__ colmax,
                                int64_t cols, int* __restrict__ ex, double* __restrict__ yd, int64_t bsy,
-                               int64_t cols_pad) {
+                               int64_t cols_pad, int* __restrict__ zero, int64_t nzero) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0)  // the product kernel's piece counters start at zero
+    for (int64_t i = c; i < nzero; i += (int64_t)gridDim.x * blockDim.x) zero[i] = 0;
   Y += (int64_t)blockIdx.y * bsy;
   colmax += (int64_t)blockIdx.y * cols_pad;
   ex += (int64_t)blockIdx.y * cols_pad;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const double* __restrict__ X_all, int64_t ldx, const double* __restrict__ Y_all, int64_t ldy,
                  const double* __restrict__ xd_all, const double* __restrict__ yd_all, int64_t ldo,
                  const __grid_constant__ Epilogue<double> epi, int* err, int64_t bsx, int64_t bsy, int64_t bse,
-                 int batch, double* __restrict__ hand) {
+                 int batch, double* __restrict__ hand, long long* __restrict__ pieces, int* __restrict__ piece_cnt) {
   constexpr int kAcc = S;  // one accumulator of BN columns per level p + q < S
   constexpr int BK = stage_k(S);
   constexpr int kSwizzleBytes = BK * 2;  // one swizzle row = one stage row
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int abort_flag;
   __shared__ __align__(8) uint64_t hand_full[2];  // a tile's sums are in scratch slot t % 2
   __shared__ __align__(8) uint64_t hand_free[2];  // the FP64 epilogue is done with the slot
+  __shared__ int hand_skip[2];  // per slot: bit w = region of draining warp w finished elsewhere
   __shared__ int kb_consumed;
   __shared__ int chunks_committed;
 
@@ -395,6 +398,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     m0 = (group * kGroupM + within % rows) * BM;
     n0 = (within / rows) * BN;
   };
+  // Work items: the whole tiles, then (with `pieces`) the tiles of the last,
+  // partial round of the persistent grid as two K halves each (split at a
+  // chunk boundary), so that the last round spreads over every CTA.  Each
+  // draining warp writes its region of a half to `pieces`; of the two CTAs
+  // that hold a region's halves, the second to count it in piece_cnt adds
+  // the other half and hands the region on, the first hands on nothing.
+  const int tail = (pieces != nullptr && num_chunks >= 2 && total > (int)gridDim.x) ? total % (int)gridDim.x : 0;
+  const int whole = total - tail;
+  const int items = whole + 2 * tail;
+  const int half_kb = (num_chunks / 2) * kChunkKb;
+  auto item_of = [&](int v, int& u, int& kb0, int& kb1, int& piece) {
+    if (v < whole) {
+      u = v;
+      kb0 = 0;
+      kb1 = num_kb;
+      piece = -1;
+    } else {
+      const int w = v - whole;
+      u = whole + (w >> 1);
+      piece = w & 1;
+      kb0 = piece ? half_kb : 0;
+      kb1 = piece ? num_kb : half_kb;
+    }
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -409,6 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int h = 0; h < 2; ++h) {
       mbar_init(&hand_full[h], kEpiWarps);
       mbar_init(&hand_free[h], kFinWarps);
+      hand_skip[h] = 0;
     }
     kb_consumed = 0;
     chunks_committed = 0;
@@ -426,10 +454,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       tma_prefetch(&mA);
       tma_prefetch(&mB);
       int g = 0;  // k-blocks issued so far, over all tiles
-      for (int u = blockIdx.x; u < total && !abort_flag; u += gridDim.x) {
+      for (int v = blockIdx.x; v < items && !abort_flag; v += gridDim.x) {
+        int u, kb0, kb1, piece;
+        item_of(v, u, kb0, kb1, piece);
         int bat, m0, n0;
         tile_of(u, bat, m0, n0);
-        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int st = g % kStages;
           if (g >= kStages && !mbar_wait(&empty_bar[st], ((g / kStages) & 1) ^ 1, &abort_flag)) {
             abort_flag = 1;
@@ -462,10 +492,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           ((kSwizzleBytes == 32 ? 6u : kSwizzleBytes == 64 ? 4u : 2u) << 29);
       int g = 0;   // k-blocks consumed so far, over all tiles
       int cg = 0;  // chunks committed so far, over all tiles
-      for (int u = blockIdx.x; u < total && !abort_flag; u += gridDim.x) {
-        int kb = 0;
-        for (int c = 0; c < num_chunks && !abort_flag; ++c, ++cg) {
-          for (int kk = 0; kk < kChunkKb && kb < num_kb; ++kk, ++kb, ++g) {
+      for (int v = blockIdx.x; v < items && !abort_flag; v += gridDim.x) {
+        int u, kb0, kb1, piece;
+        item_of(v, u, kb0, kb1, piece);
+        int kb = kb0;
+        for (int c = kb0 / kChunkKb; c * kChunkKb < kb1 && !abort_flag; ++c, ++cg) {
+          for (int kk = 0; kk < kChunkKb && kb < kb1; ++kk, ++kb, ++g) {
             const int st = g % kStages;
             if (!mbar_wait(&full_bar[st], (g / kStages) & 1, &abort_flag)) {
               abort_flag = 1;
@@ -542,9 +574,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;                // TMEM lanes 32*quarter .. +31
     const int col0 = ((warp - 2) >> 2) * kCols;  // this warp's 32 columns
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    int cg = 0;  // chunks drained so far, over all tiles
-    int t = 0;   // tiles handed over so far
-    for (int u = blockIdx.x; u < total; u += gridDim.x, ++t) {
+    const int region = quarter + 4 * ((warp - 2) >> 2);  // rows 32 quarter.., columns col0..
+    int cg = 0;  // chunks drained so far, over all items
+    int t = 0;   // items handed over so far
+    for (int v = blockIdx.x; v < items; v += gridDim.x, ++t) {
+      int u, kb0, kb1, piece;
+      item_of(v, u, kb0, kb1, piece);
       // Fixed-point sums with quantum 2^-35 of the slice products: each
       // chunk's level-L value (L <= 5) is an integer multiple of 2^(-7L) below
       // 2^24 quanta and converts exactly; levels 6, 7 are rounded to 2^-35.
@@ -553,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int j = 0; j < kCols; ++j) acc[j] = 0;
       bool ok = true;
-      for (int c = 0; c < num_chunks; ++c, ++cg) {
+      for (int c = kb0 / kChunkKb; c * kChunkKb < kb1; ++c, ++cg) {
         int w = 1;
         if (lane == 0) {
           w = mbar_wait(&chunk_bar[cg % kBufs], (cg / kBufs) & 1, &abort_flag) && !abort_flag;
@@ -585,9 +620,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      // A K half of a split tile: write this region's half; the warp that
+      // counts the region second adds the other half and hands it on.
+      bool mine = true;
+      if (ok && piece >= 0) {
+        const int q = u - whole;
+        long long* __restrict__ own = pieces + (((int64_t)q * 2 + piece) * BM + quarter * 32 + lane) * BN + col0;
+#pragma unroll
+        for (int j = 0; j < kCols; j += 2) *reinterpret_cast<longlong2*>(own + j) = make_longlong2(acc[j], acc[j + 1]);
+        __threadfence();
+        __syncwarp();
+        int second = 0;
+        if (lane == 0) second = atomicAdd(&piece_cnt[q * kEpiWarps + region], 1);
+        mine = __shfl_sync(0xffffffffu, second, 0) != 0;
+        if (mine) {
+          __threadfence();
+          const long long* other = pieces + (((int64_t)q * 2 + (1 - piece)) * BM + quarter * 32 + lane) * BN + col0;
+#pragma unroll
+          for (int j = 0; j < kCols; j += 2) {
+            const longlong2 o = __ldcg(reinterpret_cast<const longlong2*>(other + j));
+            acc[j] += o.x;
+            acc[j + 1] += o.y;
+          }
+        }
+      }
       // Hand the sums to the finishing warps through this CTA's scratch slot
-      // t % 2, once they are done with tile t - 2 there, and go on to the
-      // next tile's chunks.
+      // t % 2, once they are done with item t - 2 there, and go on to the
+      // next item's chunks (a region handed on by the other CTA is marked
+      // in hand_skip).
       if (ok && t >= 2) {
         int w = 1;
         if (lane == 0) {
@@ -597,26 +657,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       }
       if (!ok) break;
-      double* __restrict__ hrow = hand + ((int64_t)(blockIdx.x * 2 + (t & 1)) * BM + quarter * 32 + lane) * BN + col0;
+      if (mine) {
+        double* __restrict__ hrow = hand + ((int64_t)(blockIdx.x * 2 + (t & 1)) * BM + quarter * 32 + lane) * BN + col0;
 #pragma unroll
-      for (int j = 0; j < kCols; j += 2)
-        *reinterpret_cast<double2*>(hrow + j) = make_double2((double)acc[j], (double)acc[j + 1]);
-      __threadfence();  // the sums reach L2, where the finishing warps read them
+        for (int j = 0; j < kCols; j += 2)
+          *reinterpret_cast<double2*>(hrow + j) = make_double2((double)acc[j], (double)acc[j + 1]);
+        __threadfence();  // the sums reach L2, where the finishing warps read them
+      }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&hand_full[t & 1]);
+      if (lane == 0) {
+        if (mine) atomicAnd(&hand_skip[t & 1], ~(1 << region));
+        else atomicOr(&hand_skip[t & 1], 1 << region);
+        mbar_arrive(&hand_full[t & 1]);
+      }
     }
   } else {
     // FP64 epilogue of each tile from its scratch slot: warp fw walks rows
     // fw, fw + kFinWarps, ... with coalesced loads and stores.
     const int fw = warp - 2 - kEpiWarps;
     int t = 0;
-    for (int u = blockIdx.x; u < total; u += gridDim.x, ++t) {
+    for (int v = blockIdx.x; v < items; v += gridDim.x, ++t) {
+      int u, kb0, kb1, piece;
+      item_of(v, u, kb0, kb1, piece);
       int w = 1;
       if (lane == 0) {
         w = mbar_wait(&hand_full[t & 1], (t >> 1) & 1, &abort_flag) && !abort_flag;
         if (!w) abort_flag = 1;
       }
       if (!__shfl_sync(0xffffffffu, w, 0)) break;
+      // regions (row quarter, column half) that the other CTA finishes
+      const int skip = *(volatile int*)&hand_skip[t & 1];
       int bat, m0, n0;
       tile_of(u, bat, m0, n0);
       const int* __restrict__ ex = ex_all + (int64_t)bat * Mpad;
@@ -643,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int h = 0; h < BN / 32; ++h) {
           const int cl = 32 * h + lane;
           const int cc = n0 + cl;
-          if (cc >= N) continue;
+          if (cc >= N || ((skip >> ((rl >> 5) + 4 * h)) & 1)) continue;
           // P = X_off Y_off (slices) + X[r][d] Y[d][c] + X[r][c] Y[c][c] (c != d)
           const double dterm = cc != d ? xrow[cc] * yd[cc] : 0.0;
           const double p = fma(__ldcg(hslot + rl * BN + cl), pow2(er + fx[cc]), fma(xdr, yrow[cc], dterm));
@@ -773,7 +843,15 @@ OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch, int slices)
   const int64_t tiles = (int64_t)nb * (d.Mpad / BM) * (d.Npad / BN);
   d.hand_ctas = (int)std::min<int64_t>(tiles, sms);
   d.hand_bytes = al((size_t)d.hand_ctas * 2 * BM * BN * sizeof(double));
-  d.total = d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes + d.colmax_bytes + d.xd_bytes + d.yd_bytes + d.hand_bytes;
+  // the K halves of the last round's tiles (fewer than one per CTA) and a
+  // counter per region of each, when a tile has at least two 512-k chunks
+  if (tiles > d.hand_ctas && K > 512) {
+    d.split_tiles = d.hand_ctas - 1;
+    d.piece_bytes = al((size_t)d.split_tiles * 2 * BM * BN * sizeof(long long));
+    d.cnt_bytes = al((size_t)d.split_tiles * kEpiWarps * sizeof(int));
+  }
+  d.total = d.a_bytes + d.b_bytes + d.ex_bytes + d.fx_bytes + d.colmax_bytes + d.xd_bytes + d.yd_bytes + d.hand_bytes +
+            d.piece_bytes + d.cnt_bytes;
   return d;
 }
 
@@ -794,6 +872,8 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   double* xd = (double*)((char*)colmax + d.colmax_bytes);
   double* yd = (double*)((char*)xd + d.xd_bytes);
   double* hand = (double*)((char*)yd + d.yd_bytes);
+  long long* pieces = (long long*)((char*)hand + d.hand_bytes);
+  int* piece_cnt = (int*)((char*)pieces + d.piece_bytes);
   const unsigned nb = (unsigned)batch;
   {
     ProfScope prof(CS_KERNEL_OTHER, (double)batch * (double)(M * K + K * N) * (8.0 + 2.0 * S), stream);
@@ -801,7 +881,8 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
     CS_CUDA_CHECK(cudaMemsetAsync(colmax, 0, d.colmax_bytes, stream));
     col_max_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)((K + 255) / 256), nb), 256, 0, stream>>>(
         Y, K, N, ldy, colmax, bsy, d.Npad);
-    col_exp_kernel<<<dim3((unsigned)((N + 255) / 256), nb), 256, 0, stream>>>(Y, ldy, colmax, N, fx, yd, bsy, d.Npad);
+    col_exp_kernel<<<dim3((unsigned)((N + 255) / 256), nb), 256, 0, stream>>>(
+        Y, ldy, colmax, N, fx, yd, bsy, d.Npad, piece_cnt, (int64_t)(d.cnt_bytes / sizeof(int)));
     const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(d.Mpad * d.ldk), 152 * 16 / batch + 1));
     slice_rows_kernel<S><<<dim3(sgrid, nb), 256, 0, stream>>>(X, M, K, ldx, ex, a_sl, d.Mpad, d.ldk, bsx);
     slice_cols_kernel<S><<<dim3((unsigned)(d.Npad / 32), (unsigned)(d.ldk / 32), nb), 256, 0, stream>>>(
@@ -821,9 +902,14 @@ cs_status launch_emu(const double* X, const double* Y, int64_t M, int64_t N, int
   CS_CUDA_CHECK(cudaGetDevice(&dev));
   CS_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = (unsigned)std::min<int64_t>(std::min<int64_t>(tiles, sms > 0 ? sms : 1), d.hand_ctas);
+  // the last round's tiles split in K halves (the kernel takes tiles % grid
+  // of them; col_exp_kernel zeroed their counters)
+  const bool split = d.split_tiles > 0 && tiles > (int64_t)grid && tiles % grid != 0 &&
+                     (int64_t)(tiles % grid) <= d.split_tiles;
   ozaki_kernel<S><<<grid, kThreads, kSmem, stream>>>(mA, mB, (int)M, (int)N, (int)K, (int)d.Mpad, (int)d.Npad, ex,
                                                      fx, X, ldx, Y, ldy, xd, yd, ldo, epi, err, bsx, bsy, bse,
-                                                     (int)batch, hand);
+                                                     (int)batch, hand, split ? pieces : nullptr,
+                                                     split ? piece_cnt : nullptr);
   CS_CUDA_CHECK(cudaGetLastError());
   return CS_OK;
 }

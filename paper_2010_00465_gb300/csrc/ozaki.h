@@ -18,13 +18,16 @@ constexpr int kOzakiSlicesSplit = 4;
 constexpr int64_t kOzakiMaxK = 8192;  // inner dimension limit of the int64 sums
 
 // Scratch of one emulated product: the BF16 slices of both operands, their
-// row / column exponents, the column maxima, and two tiles of sums per CTA of
-// the product kernel (at most one per SM of the current device).
+// row / column exponents, the column maxima, two tiles of sums per CTA of the
+// product kernel (at most one per SM of the current device), and the K
+// halves of the tiles of its last round.
 struct OzakiDims {
   int64_t Mpad = 0, Npad = 0, ldk = 0;
   size_t a_bytes = 0, b_bytes = 0, ex_bytes = 0, fx_bytes = 0, colmax_bytes = 0, xd_bytes = 0, yd_bytes = 0;
   size_t hand_bytes = 0;
   int hand_ctas = 0;
+  int64_t split_tiles = 0;  // at most this many last-round tiles split in K halves
+  size_t piece_bytes = 0, cnt_bytes = 0;
   size_t total = 0;
 };
 OzakiDims ozaki_dims(int64_t M, int64_t N, int64_t K, int64_t batch = 1, int slices = kOzakiSlices);
