@@ -76,6 +76,14 @@
 //              four-slice one's; four warps still held up the four-slice
 //              kernel, as the epilogue's FP64 operations are long-latency
 //              on GB300).
+// Last round: a persistent grid of G CTAs over T tiles runs ceil(T / G)
+// rounds, the last one partial (2048 tiles of an n = 4096 product are 13.5
+// rounds of 152).  Those T mod G tiles run as two K halves each (split at a
+// 512-k chunk boundary) on different CTAs; each draining warp writes its
+// 32 x 32 region's int64 half to the workspace and counts the region, and
+// the warp that counts it second adds the other half (the sum stays exact)
+// and hands the region on, while the first hands on nothing.  No CTA waits
+// for another.
 // Every mbarrier wait is bounded; on expiry the CTA stops issuing, waits
 // (bounded) for what it issued, frees TMEM and raises *err.
 #include <cuda.h>
