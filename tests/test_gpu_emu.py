@@ -50,6 +50,26 @@ def test_product_bound(n):
     assert relfro(P, ref) <= 1e-15
 
 
+@pytest.mark.parametrize("n", [1152, 1300])
+@pytest.mark.parametrize("slices", [8, 4])
+def test_product_split_last_round(n, slices):
+    """More tiles than a 152-SM GB300 runs at once and K over two 512-k chunks:
+    the persistent grid's last, partial round runs as K halves on different
+    CTAs (1152: 162 tiles, halves of one and two chunks; 1300: ragged edges)
+    and must still meet the product's bound everywhere."""
+    X = inputs.matrix(n, "normal", None, index=196, sub=n)
+    Y = inputs.matrix(n, "normal", None, index=197, sub=n)
+    if slices == 8:
+        check_product(X, Y)
+        return
+    P = api.matmul(dev(X), dev(Y), "split_bf16").cpu().numpy()
+    ref = oracle.matmul(X, Y)
+    rowmax = np.abs(X).max(axis=1, keepdims=True)
+    colmax = np.abs(Y).max(axis=0, keepdims=True)
+    bound = 4 * n * U * (np.abs(X) @ np.abs(Y)) + 2.0 ** -25 * n * rowmax * colmax
+    assert np.all(np.abs(P - ref) <= bound), float(np.max(np.abs(P - ref) / bound))
+
+
 def test_product_long_k():
     """K = 1536 spans three promotion chunks of 512."""
     n = 1536
