@@ -166,6 +166,23 @@ def test_emulated_control_workload_sampled():
         assert relfro(dA[b], oracle.gradient(A[b], GC[b], GS[b], m, s)) <= TOL64
 
 
+def test_emulated_batched_split_last_round():
+    """Four matrices of order 640 (200 emulated product tiles over a 152-SM
+    grid, K over two 512-k chunks): the batched products' last round runs as
+    K halves, spread over matrices of the batch; the gradient must match the
+    native FP64 adjoint and, for one matrix, the oracle."""
+    count, n = 4, 640
+    A = np.stack([inputs.matrix(n, "normal", 3.0, index=125, sub=i + 1) for i in range(count)])
+    GC = np.stack([inputs.matrix(n, "normal", None, index=126, sub=i + 1) for i in range(count)])
+    GS = np.stack([inputs.matrix(n, "normal", None, index=127, sub=i + 1) for i in range(count)])
+    dA = api.cossin_backward(cuda(A), cuda(GC), cuda(GS), prec="fp64_emu").cpu().numpy()
+    dA64 = api.cossin_backward(cuda(A), cuda(GC), cuda(GS)).cpu().numpy()
+    for b in range(count):
+        assert relfro(dA[b], dA64[b]) <= 1e-11
+    m, s = oracle.select(oracle.norm1(A[3]), "double")
+    assert relfro(dA[3], oracle.gradient(A[3], GC[3], GS[3], m, s)) <= TOL64
+
+
 def test_emulated_adjoint_argument_errors():
     A = torch.zeros(3, 3, dtype=torch.float64, device="cuda")
     with pytest.raises(_lib.CossinError) as ex:
