@@ -22,7 +22,8 @@
 //     ping-pong, so the tensor pipe keeps running while one is drained).
 //     Promoting every 32 k kept the error at 1.4e-7 (K = 4096) but the MMAs
 //     then waited for the drains: 1.09 ms per n = 4096 product against
-//     0.95 ms every 64 k (2.0e-7) and 0.84 ms every 128 k (3.4e-7).
+//     0.95 ms every 64 k (2.0e-7), 0.84 ms every 128 k (3.4e-7) and 0.78 ms
+//     every 256 k (6.4e-7, not taken: the error nearly doubles for 6 %).
 //
 // One CTA computes a 128 x 128 tile:
 //   warp 0     TMA producer: X_hi, X_lo (128 x 32) and Y^T_hi, Y^T_lo
